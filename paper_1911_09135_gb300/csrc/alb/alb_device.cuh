@@ -1,0 +1,83 @@
+// Device helpers shared by the round kernels: warp-aggregated appends, warp and
+// block scans, and the last-block ticket used to finish a round on the device.
+#pragma once
+
+#include "alb_internal.cuh"
+
+namespace alb {
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+// Warp-aggregated append of `v` for every lane with `pred`: one atomicAdd on
+// `count` per warp (ballot + popc), lanes write consecutive slots. Every lane of
+// the warp must call it (the callers keep their loops warp-uniform).
+__device__ __forceinline__ void warp_append(bool pred, uint32_t v, uint32_t* buf, uint32_t* count) {
+  const unsigned mask = __ballot_sync(kFull, pred);
+  if (mask == 0) return;
+  const uint32_t lane = lane_id();
+  const uint32_t leader = __ffs(mask) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(mask));
+  base = __shfl_sync(kFull, base, leader);
+  if (pred) buf[base + __popc(mask & ((1u << lane) - 1u))] = v;
+}
+
+// Inclusive warp scan (Kogge-Stone over shuffles).
+__device__ __forceinline__ uint32_t warp_inclusive_scan(uint32_t x) {
+  const uint32_t lane = lane_id();
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, x, o);
+    if (lane >= (uint32_t)o) x += y;
+  }
+  return x;
+}
+
+// Exclusive scan over the CTA; *total receives the CTA sum. Uses s_warp[kWarps]
+// and synchronises the CTA (every thread must call it).
+template <int BLOCK>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* s_warp, uint32_t* total) {
+  constexpr int W = BLOCK / 32;
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  const uint32_t incl = warp_inclusive_scan(x);
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t t = lane < (uint32_t)W ? s_warp[lane] : 0u;
+    const uint32_t ti = warp_inclusive_scan(t);
+    if (lane < (uint32_t)W) s_warp[lane] = ti - t;  // exclusive warp offsets
+    if (lane == 31) s_warp[W] = ti;
+  }
+  __syncthreads();
+  const uint32_t res = s_warp[warp] + incl - x;
+  *total = s_warp[W];
+  __syncthreads();
+  return res;
+}
+
+// Last-block ticket: every CTA calls this once at its end (all threads). Returns
+// true in exactly one thread of the CTA that arrives last; that thread then
+// sees every other CTA's writes (fence before the ticket, L2 reads after).
+__device__ __forceinline__ bool last_block_ticket(uint32_t* counter) {
+  __shared__ uint32_t s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const uint32_t t = atomicAdd(counter, 1u);
+    s_last = (t == gridDim.x - 1) ? 1u : 0u;
+    if (s_last) __threadfence();
+  }
+  __syncthreads();
+  return s_last && threadIdx.x == 0;
+}
+
+// Largest j in [lo, hi) with P[j] <= k, given P[lo] <= k and (implicitly) P[hi] > k.
+__device__ __forceinline__ uint32_t upper_search(const uint32_t* P, uint32_t lo, uint32_t hi, uint32_t k) {
+  while (hi - lo > 1) {
+    const uint32_t mid = lo + ((hi - lo) >> 1);
+    if (P[mid] <= k) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+}  // namespace alb

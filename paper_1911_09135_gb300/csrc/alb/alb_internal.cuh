@@ -1,0 +1,160 @@
+// Internal declarations of libalb.so: device-side round state, the kernel
+// context passed by value to every round kernel, and the host-side graph handle.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+
+#include "alb.h"
+
+namespace alb {
+
+constexpr uint32_t kInf = 0xFFFFFFFFu;
+constexpr int kBlock = 256;             // threads per CTA of every round kernel
+constexpr int kWarps = kBlock / 32;
+constexpr int kHubSmem = 2048;          // huge vertices the LB kernel stages in shared memory
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+
+// Latched device error bits.
+enum : uint32_t { ST_ERR_ROUNDS = 1u, ST_ERR_INDEX = 2u };
+
+enum App : int { APP_BFS = 0, APP_SSSP = 1, APP_CC = 2, APP_KCORE = 3, APP_TRACE = 4, APP_COUNT = 5 };
+
+// Device-resident state of one traversal, zeroed before each call.
+struct RoundState {
+  uint32_t round;                  // current round r
+  uint32_t fcount[2];              // frontier sizes, indexed by round parity
+  uint32_t tile_next;              // dynamic tile counter of the inspection kernel
+  unsigned long long hub_packed;   // (huge count << 32) | huge edge total, one atomic per warp
+  uint32_t done_inspect;           // last-block tickets
+  uint32_t done_lb;
+  uint32_t status;                 // ST_ERR_* bits
+  uint32_t all_active;             // round 0 of cc: the frontier is every vertex
+  uint32_t hub_rounds;
+  uint32_t max_hub_count;
+  unsigned long long edges_twc;
+  unsigned long long edges_lb;
+  unsigned long long pushes;
+};
+
+// Per-call arguments, written on the stream by a one-thread kernel before the
+// (cached) CUDA graph of the application is launched.
+struct CallArgs {
+  uint32_t* lab;      // labels being computed (levels, dist, labels, remaining degree)
+  uint32_t src;
+  uint32_t k;         // kcore
+  uint32_t* trace_src;
+  uint32_t* trace_dst;
+  uint32_t* trace_thread;
+};
+
+// Everything a round kernel needs, passed by value (fixed for a cached graph).
+struct TravCtx {
+  const uint32_t* off;
+  const uint32_t* idx;
+  const uint32_t* w;
+  uint32_t n;
+  uint32_t threshold;     // degree >= threshold: huge (Algorithm 1)
+  uint32_t warp_min;      // TWC warp bin lower bound
+  uint32_t cta_min;       // TWC CTA bin lower bound
+  uint32_t distribution;  // 0 cyclic, 1 blocked (Algorithm 2)
+  uint32_t max_rounds;
+  uint32_t use_graph;     // conditional handles valid
+  uint32_t pad;
+  uint32_t* F0;           // frontier buffers (round parity 0 / 1)
+  uint32_t* F1;
+  uint32_t* hub_v;        // huge worklist "work"
+  uint32_t* hub_p;        // exclusive prefix sum of huge degrees ("prefixWork")
+  uint32_t* stamp;        // round stamps: dedup of next-frontier pushes (sssp, cc)
+  RoundState* st;
+  const CallArgs* args;
+  cudaGraphConditionalHandle h_while;
+  cudaGraphConditionalHandle h_if;
+};
+
+}  // namespace alb
+
+// Host-side handle.
+struct alb_graph_s {
+  int device = 0;
+  uint32_t n = 0;
+  uint64_t m = 0;
+  uint32_t flags = 0;
+  bool has_w = false;
+  uint32_t max_w = 0;
+  uint32_t max_deg = 0;
+  uint32_t* off = nullptr;
+  uint32_t* idx = nullptr;
+  uint32_t* w = nullptr;
+
+  alb_params params{};
+  int num_sms = 0;
+  uint32_t blocks = 0;        // CTAs of the inspection / init kernels (persistent grid)
+  uint32_t lb_blocks = 0;     // CTAs of the LB kernel (its threads are the default threshold)
+  uint32_t threshold = 0;     // effective huge threshold
+
+  // traversal workspace
+  uint32_t* F0 = nullptr;
+  uint32_t* F1 = nullptr;
+  uint32_t* hub_v = nullptr;
+  uint32_t* hub_p = nullptr;
+  uint32_t* stamp = nullptr;
+  uint32_t* tmp = nullptr;        // n-entry scratch output when the caller's buffer is host memory
+  alb::RoundState* st = nullptr;
+  alb::CallArgs* args = nullptr;
+  alb::RoundState* h_st = nullptr;  // pinned mirror
+
+  cudaGraph_t graph[alb::APP_COUNT] = {};
+  cudaGraphExec_t exec[alb::APP_COUNT] = {};
+
+  cudaStream_t last_stream = nullptr;
+  int last_kind = -1;            // 0 traversal, 1 pagerank
+  alb_status latched = ALB_OK;
+  alb_stats stats{};
+
+  // pagerank workspace (alb_pagerank.cu)
+  struct PrWs* pr = nullptr;
+  // batch workspace (alb_batch.cu)
+  struct BatchWs* batch = nullptr;
+};
+
+namespace alb {
+
+// ---- helpers shared by the host translation units -----------------------------------------
+#define ALB_CUDA_TRY(expr)                                                   \
+  do {                                                                       \
+    cudaError_t _e = (expr);                                                 \
+    if (_e != cudaSuccess) {                                                 \
+      if (std::getenv("ALB_DEBUG"))                                          \
+        std::fprintf(stderr, "libalb: %s failed: %s (%s:%d)\n", #expr,       \
+                     cudaGetErrorString(_e), __FILE__, __LINE__);            \
+      return (_e == cudaErrorMemoryAllocation) ? ALB_ERR_OOM : ALB_ERR_CUDA; \
+    }                                                                        \
+  } while (0)
+
+bool is_device_ptr(const void* p);
+alb_status ensure_tmp(alb_graph g);
+alb_status traversal_status(alb_graph g);   // reads h_st after a sync
+alb_status free_traversal_graphs(alb_graph g);
+alb_status free_pagerank(alb_graph g);
+alb_status free_batch(alb_graph g);
+TravCtx make_ctx(alb_graph g, bool use_graph, cudaGraphConditionalHandle hw,
+                 cudaGraphConditionalHandle hi);
+alb_status run_traversal(alb_graph g, App app, uint32_t src, uint32_t k, uint32_t* out,
+                         cudaStream_t s);
+alb_status launch_lb_trace(alb_graph g, const uint32_t* d_work, const uint32_t* d_prefix,
+                           uint32_t nwork, uint32_t* d_src, uint32_t* d_dst, uint32_t* d_thread,
+                           cudaStream_t s);
+alb_status launch_inspect_only(alb_graph g, const uint32_t* d_wl, uint32_t nf, uint8_t* d_bin,
+                               uint32_t* d_work, uint32_t* d_prefix, uint32_t* d_counts,
+                               cudaStream_t s);
+void occupancy(uint32_t* inspect_per_sm, uint32_t* lb_per_sm);
+alb_status pr_stats(alb_graph g, alb_stats* out);
+alb_status batch_stats(alb_graph g, alb_stats* out);
+alb_status latch_from_state(alb_graph g, uint32_t status);
+uint32_t effective_threshold(alb_graph g);
+
+}  // namespace alb

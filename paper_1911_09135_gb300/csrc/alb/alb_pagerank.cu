@@ -1,0 +1,644 @@
+// PageRank with the adaptive load balancer (arXiv:1911.09135, Sec. 5 "pr":
+// pull over incoming edges; on a symmetric graph the CSR rows are the in-edge
+// lists). pr is topology-driven: every vertex is active in every iteration, so
+// the inspection of Algorithm 1 runs once per graph and its bins are reused:
+//   - huge vertices (degree >= threshold): their in-edges are dealt cyclically
+//     over every thread of the grid (Algorithm 2); each warp covers 32
+//     consecutive positions and reduces them per source vertex, writing one
+//     partial per (32-position chunk, vertex) pair into its own slot; a second
+//     kernel sums each vertex's partials in chunk order;
+//   - CTA / warp / thread bins: one CTA / warp / thread forms a vertex's sum.
+// All sums have a fixed order, so the result is bit-reproducible. Values and
+// sums are FP32; the L1 change that decides convergence is summed in FP64.
+//
+// Recurrence (N = n, deg = out-degree, D_t = mass on degree-0 vertices):
+//   x_0 = 1/N,  x_{t+1}[v] = (1-d)/N + d * (sum_{u->v} x_t[u]/deg(u) + D_t/N).
+#include <new>
+
+#include "alb_device.cuh"
+
+namespace alb {
+
+constexpr uint32_t kPartChunk = 4096;  // vertices per CTA in the stable partition
+
+struct PrState {
+  uint32_t iter;
+  uint32_t status;
+  double l1;
+  float dangling;  // D_t of the current iterate
+  float pad;
+};
+
+struct PrArgs {
+  float* rank;
+  float damping;
+  double tol;
+  uint32_t max_iter;
+  double* l1_out;      // device pointer or null
+  uint32_t* iters_out; // device pointer or null
+};
+
+struct PrCtx {
+  const uint32_t* off;
+  const uint32_t* idx;
+  uint32_t n;
+  uint32_t nh, nc, nw, ns;     // bin sizes
+  const uint32_t* hubs;        // bin lists, each in vertex order
+  const uint32_t* ctas;
+  const uint32_t* warps;
+  const uint32_t* smalls;
+  const uint32_t* hub_p;       // exclusive prefix of hub degrees (nh + 1)
+  uint32_t e;                  // hub edges
+  float* x[2];
+  float* cb[2];                // x / deg (0 for deg 0)
+  float* part;                 // hub partial slots
+  double* l1_part;             // per pull-CTA, then per hub
+  float* dang_part;
+  uint32_t pull_blocks;
+  PrState* st;
+  const PrArgs* args;
+  cudaGraphConditionalHandle h_while;
+  uint32_t use_graph;
+};
+
+}  // namespace alb
+
+struct PrWs {
+  bool ready = false;
+  uint32_t nh = 0, nc = 0, nw = 0, ns = 0, e = 0, zero_deg = 0;
+  uint32_t* lists = nullptr;   // n entries: hubs | ctas | warps | smalls
+  uint32_t* hub_p = nullptr;
+  uint32_t* cnt = nullptr;     // per-partition-block bin counts
+  float* x0 = nullptr;
+  float* x1 = nullptr;
+  float* c0 = nullptr;
+  float* c1 = nullptr;
+  float* part = nullptr;
+  double* l1_part = nullptr;
+  float* dang_part = nullptr;
+  alb::PrState* st = nullptr;
+  alb::PrState* h_st = nullptr;
+  alb::PrArgs* args = nullptr;
+  float* tmp_rank = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace alb {
+
+__device__ __forceinline__ uint32_t pr_bin(uint32_t deg, uint32_t t, uint32_t wmin, uint32_t cmin) {
+  if (deg >= t) return 0u;    // huge
+  if (deg >= cmin) return 1u; // CTA
+  if (deg >= wmin) return 2u; // warp
+  return 3u;                  // thread
+}
+
+// ---- one-time inspection: stable partition of all vertices into the 4 bins
+
+__global__ void __launch_bounds__(kBlock) k_pr_count(const uint32_t* off, uint32_t n, uint32_t t,
+                                                     uint32_t wmin, uint32_t cmin, uint32_t* cnt) {
+  __shared__ uint32_t s[5];
+  if (threadIdx.x < 5) s[threadIdx.x] = 0u;
+  __syncthreads();
+  const uint64_t lo = (uint64_t)blockIdx.x * kPartChunk;
+  const uint64_t hi = lo + kPartChunk < n ? lo + kPartChunk : n;
+  uint32_t c[5] = {0, 0, 0, 0, 0};
+  for (uint64_t v = lo + threadIdx.x; v < hi; v += kBlock) {
+    const uint32_t d = off[v + 1] - off[v];
+    c[pr_bin(d, t, wmin, cmin)]++;
+    if (d == 0) c[4]++;
+  }
+  for (int b = 0; b < 5; ++b) if (c[b]) atomicAdd(&s[b], c[b]);
+  __syncthreads();
+  if (threadIdx.x < 5) cnt[blockIdx.x * 5 + threadIdx.x] = s[threadIdx.x];
+}
+
+// Exclusive scan of the per-block counts of each bin (one CTA, serial over blocks per bin).
+__global__ void k_pr_scan_counts(uint32_t* cnt, uint32_t nblk, uint32_t* totals) {
+  if (threadIdx.x < 5) {
+    const uint32_t b = threadIdx.x;
+    uint32_t run = 0;
+    for (uint32_t i = 0; i < nblk; ++i) {
+      const uint32_t c = cnt[i * 5 + b];
+      cnt[i * 5 + b] = run;
+      run += c;
+    }
+    totals[b] = run;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_pr_scatter(const uint32_t* off, uint32_t n, uint32_t t,
+    uint32_t wmin, uint32_t cmin, const uint32_t* cnt, uint32_t* lists, uint32_t nh, uint32_t nc,
+    uint32_t nw) {
+  __shared__ uint32_t s_warp[kWarps + 1];
+  __shared__ uint32_t s_base[4];
+  const uint32_t bin_start[4] = {0u, nh, nh + nc, nh + nc + nw};
+  if (threadIdx.x < 4) s_base[threadIdx.x] = bin_start[threadIdx.x] + cnt[blockIdx.x * 5 + threadIdx.x];
+  __syncthreads();
+  const uint64_t lo = (uint64_t)blockIdx.x * kPartChunk;
+  const uint64_t hi = lo + kPartChunk < n ? lo + kPartChunk : n;
+  for (uint64_t b0 = lo; b0 < hi; b0 += kBlock) {
+    const uint64_t v = b0 + threadIdx.x;
+    const bool ok = v < hi;
+    const uint32_t bin = ok ? pr_bin(off[v + 1] - off[v], t, wmin, cmin) : 4u;
+    for (uint32_t b = 0; b < 4; ++b) {
+      uint32_t tot;
+      const uint32_t rank = block_exclusive_scan<kBlock>(bin == b ? 1u : 0u, s_warp, &tot);
+      if (bin == b) lists[s_base[b] + rank] = (uint32_t)v;
+      __syncthreads();
+      if (threadIdx.x == 0) s_base[b] += tot;
+      __syncthreads();
+    }
+  }
+}
+
+// prefix[j] = sum of degrees of hubs[0..j), prefix[nh] = e (one CTA, carried scan).
+__global__ void k_pr_hub_prefix(const uint32_t* off, const uint32_t* hubs, uint32_t nh,
+                                uint32_t* prefix) {
+  __shared__ uint32_t s_warp[kWarps + 1];
+  __shared__ uint32_t s_carry;
+  if (threadIdx.x == 0) s_carry = 0u;
+  __syncthreads();
+  for (uint32_t b0 = 0; b0 < nh; b0 += kBlock) {
+    const uint32_t j = b0 + threadIdx.x;
+    const uint32_t d = j < nh ? off[hubs[j] + 1] - off[hubs[j]] : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_exclusive_scan<kBlock>(d, s_warp, &tot);
+    if (j < nh) prefix[j] = s_carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) prefix[nh] = s_carry;
+}
+
+// ---- iteration kernels
+
+__global__ void __launch_bounds__(kBlock) k_pr_init(PrCtx c, float dangling0) {
+  const float x0 = 1.0f / (float)c.n;
+  for (uint64_t v = (uint64_t)blockIdx.x * kBlock + threadIdx.x; v < c.n; v += (uint64_t)gridDim.x * kBlock) {
+    const uint32_t d = c.off[v + 1] - c.off[v];
+    c.x[0][v] = x0;
+    c.cb[0][v] = d ? x0 / (float)d : 0.0f;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    c.st->iter = 0u;
+    c.st->dangling = dangling0;
+    c.st->l1 = 0.0;
+  }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// Writes x_{t+1}[v], its contribution, and accumulates |x_{t+1} - x_t| and the new
+// dangling mass in the calling thread's accumulators.
+__device__ __forceinline__ void pr_update(const PrCtx& c, uint32_t v, uint32_t deg, float s,
+                                          float base, float d, uint32_t par, double& l1, float& dang) {
+  const float xn = base + d * s;
+  c.x[par ^ 1u][v] = xn;
+  c.cb[par ^ 1u][v] = deg ? xn / (float)deg : 0.0f;
+  l1 += fabs((double)xn - (double)c.x[par][v]);
+  if (deg == 0) dang += xn;
+}
+
+template <int BLOCK>
+__device__ __forceinline__ void block_reduce_store(double l1, float dang, double* l1_out, float* dang_out) {
+  __shared__ double s_l1[BLOCK / 32];
+  __shared__ float s_d[BLOCK / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    l1 += __shfl_xor_sync(kFull, l1, o);
+    dang += __shfl_xor_sync(kFull, dang, o);
+  }
+  const uint32_t warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { s_l1[warp] = l1; s_d[warp] = dang; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    float b = 0.0f;
+    for (int w = 0; w < BLOCK / 32; ++w) { a += s_l1[w]; b += s_d[w]; }
+    *l1_out = a;
+    *dang_out = b;
+  }
+}
+
+// CTA, warp and thread bins (static assignment, fixed reduction order).
+__global__ void __launch_bounds__(kBlock) k_pr_pull(PrCtx c) {
+  __shared__ float s_red[kWarps];
+  const PrArgs* pa = c.args;
+  const float d = pa->damping;
+  const uint32_t par = c.st->iter & 1u;
+  const float N = (float)c.n;
+  const float base = (1.0f - d) / N + d * (c.st->dangling / N);
+  const float* cb = c.cb[par];
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  double l1 = 0.0;
+  float dang = 0.0f;
+  // CTA bin: the CTA sums one vertex's in-edges
+  for (uint32_t j = blockIdx.x; j < c.nc; j += gridDim.x) {
+    const uint32_t v = c.ctas[j];
+    const uint32_t b = c.off[v], deg = c.off[v + 1] - b;
+    float s = 0.0f;
+    for (uint32_t e = tid; e < deg; e += kBlock) s += cb[__ldg(c.idx + b + e)];
+    s = warp_sum(s);
+    if (lane == 0) s_red[warp] = s;
+    __syncthreads();
+    if (tid == 0) {
+      float t = 0.0f;
+      for (int w = 0; w < kWarps; ++w) t += s_red[w];
+      pr_update(c, v, deg, t, base, d, par, l1, dang);
+    }
+    __syncthreads();
+  }
+  // warp bin
+  const uint32_t gw = blockIdx.x * kWarps + warp, nwarps = gridDim.x * kWarps;
+  for (uint32_t j = gw; j < c.nw; j += nwarps) {
+    const uint32_t v = c.warps[j];
+    const uint32_t b = c.off[v], deg = c.off[v + 1] - b;
+    float s = 0.0f;
+    for (uint32_t e = lane; e < deg; e += 32) s += cb[__ldg(c.idx + b + e)];
+    s = warp_sum(s);
+    if (lane == 0) pr_update(c, v, deg, s, base, d, par, l1, dang);
+  }
+  // thread bin
+  const uint32_t gt = blockIdx.x * kBlock + tid, nthreads = gridDim.x * kBlock;
+  for (uint32_t j = gt; j < c.ns; j += nthreads) {
+    const uint32_t v = c.smalls[j];
+    const uint32_t b = c.off[v], deg = c.off[v + 1] - b;
+    float s = 0.0f;
+    for (uint32_t e = 0; e < deg; ++e) s += cb[__ldg(c.idx + b + e)];
+    pr_update(c, v, deg, s, base, d, par, l1, dang);
+  }
+  block_reduce_store<kBlock>(l1, dang, c.l1_part + blockIdx.x, c.dang_part + blockIdx.x);
+}
+
+// Huge vertices, cyclic over all threads: per-warp segmented sums into slots.
+__global__ void __launch_bounds__(kBlock) k_pr_hub(PrCtx c) {
+  __shared__ uint32_t s_p[kHubSmem];
+  __shared__ uint32_t s_base[kHubSmem];
+  const uint32_t nh = c.nh, e = c.e;
+  const bool staged = nh <= (uint32_t)kHubSmem;
+  if (staged) {
+    for (uint32_t j = threadIdx.x; j < nh; j += kBlock) {
+      const uint32_t p = c.hub_p[j];
+      s_p[j] = p;
+      s_base[j] = c.off[c.hubs[j]] - p;
+    }
+  }
+  __syncthreads();
+  const uint32_t* P = staged ? s_p : c.hub_p;
+  const float* cb = c.cb[c.st->iter & 1u];
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t p = (uint64_t)gridDim.x * kBlock;
+  const uint64_t gt = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
+  uint32_t j = 0u;
+  for (uint64_t k0 = gt - lane; k0 < e; k0 += p) {  // warp-uniform; lane takes k0 + lane
+    const uint64_t k = k0 + lane;
+    const bool ok = k < e;
+    float val = 0.0f;
+    uint32_t jj = kInf;
+    if (ok) {
+      j = upper_search(P, j, nh, (uint32_t)k);
+      jj = j;
+      const uint32_t base = staged ? s_base[j] : c.off[c.hubs[j]] - c.hub_p[j];
+      val = cb[__ldg(c.idx + (uint32_t)k + base)];
+    }
+    // segmented inclusive scan by hub index (positions are consecutive in the warp)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float y = __shfl_up_sync(kFull, val, o);
+      const uint32_t jy = __shfl_up_sync(kFull, jj, o);
+      if (lane >= (uint32_t)o && jy == jj) val += y;
+    }
+    const uint32_t jn = __shfl_down_sync(kFull, jj, 1);
+    const bool tail = ok && (lane == 31 || jn != jj);
+    if (tail) c.part[(uint32_t)(k0 >> 5) + jj] = val;
+  }
+}
+
+// One warp per huge vertex: sum its slots in chunk order, then update.
+__global__ void __launch_bounds__(kBlock) k_pr_hub_fin(PrCtx c) {
+  const PrArgs* pa = c.args;
+  const float d = pa->damping;
+  const uint32_t par = c.st->iter & 1u;
+  const float N = (float)c.n;
+  const float base = (1.0f - d) / N + d * (c.st->dangling / N);
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t gw = (blockIdx.x * kBlock + threadIdx.x) >> 5, nwarps = (gridDim.x * kBlock) >> 5;
+  for (uint32_t j = gw; j < c.nh; j += nwarps) {
+    const uint32_t v = c.hubs[j];
+    const uint32_t p0 = c.hub_p[j], p1 = c.hub_p[j + 1];
+    float s = 0.0f;
+    if (p1 > p0) {
+      const uint32_t w0 = p0 >> 5, w1 = (p1 - 1) >> 5;
+      for (uint32_t w = w0 + lane; w <= w1; w += 32) s += c.part[w + j];
+    }
+    s = warp_sum(s);
+    double l1 = 0.0;
+    float dang = 0.0f;
+    if (lane == 0) {
+      pr_update(c, v, p1 - p0, s, base, d, par, l1, dang);
+      c.l1_part[c.pull_blocks + j] = l1;
+      c.dang_part[c.pull_blocks + j] = dang;
+    }
+  }
+}
+
+// Reduce the partials in a fixed order, advance the iteration, set the loop condition.
+__global__ void k_pr_finalize(PrCtx c) {
+  __shared__ double s_l1[kWarps];
+  __shared__ float s_d[kWarps];
+  const uint32_t np = c.pull_blocks + c.nh;
+  double l1 = 0.0;
+  float dg = 0.0f;
+  for (uint32_t i = threadIdx.x; i < np; i += kBlock) { l1 += c.l1_part[i]; dg += c.dang_part[i]; }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    l1 += __shfl_xor_sync(kFull, l1, o);
+    dg += __shfl_xor_sync(kFull, dg, o);
+  }
+  if ((threadIdx.x & 31) == 0) { s_l1[threadIdx.x >> 5] = l1; s_d[threadIdx.x >> 5] = dg; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    float b = 0.0f;
+    for (int w = 0; w < kWarps; ++w) { a += s_l1[w]; b += s_d[w]; }
+    PrState* st = c.st;
+    const PrArgs* pa = c.args;
+    st->l1 = a;
+    st->dangling = b;
+    st->iter += 1u;
+    const bool go = !(a < pa->tol) && st->iter < pa->max_iter;
+    if (c.use_graph) cudaGraphSetConditional(c.h_while, go ? 1u : 0u);
+  }
+}
+
+__global__ void k_pr_output(PrCtx c) {
+  const PrArgs* pa = c.args;
+  const uint32_t par = c.st->iter & 1u;
+  const float* x = c.x[par];
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < c.n;
+       v += (uint64_t)gridDim.x * blockDim.x)
+    pa->rank[v] = x[v];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (pa->l1_out) *pa->l1_out = c.st->l1;
+    if (pa->iters_out) *pa->iters_out = c.st->iter;
+  }
+}
+
+__global__ void k_pr_set_args(PrArgs* dst, PrArgs v) { *dst = v; }
+
+// ---------------------------------------------------------------- host side
+
+alb_status free_pagerank(alb_graph g) {
+  PrWs* w = g->pr;
+  if (!w) return ALB_OK;
+  if (w->exec) cudaGraphExecDestroy(w->exec);
+  if (w->graph) cudaGraphDestroy(w->graph);
+  cudaFree(w->lists); cudaFree(w->hub_p); cudaFree(w->cnt);
+  cudaFree(w->x0); cudaFree(w->x1); cudaFree(w->c0); cudaFree(w->c1);
+  cudaFree(w->part); cudaFree(w->l1_part); cudaFree(w->dang_part);
+  cudaFree(w->st); cudaFree(w->args); cudaFree(w->tmp_rank);
+  if (w->h_st) cudaFreeHost(w->h_st);
+  cudaGetLastError();
+  delete w;
+  g->pr = nullptr;
+  return ALB_OK;
+}
+
+static PrCtx pr_ctx(alb_graph g, bool use_graph, cudaGraphConditionalHandle hw) {
+  PrWs* w = g->pr;
+  PrCtx c{};
+  c.off = g->off;
+  c.idx = g->idx;
+  c.n = g->n;
+  c.nh = w->nh; c.nc = w->nc; c.nw = w->nw; c.ns = w->ns;
+  c.hubs = w->lists;
+  c.ctas = w->lists + w->nh;
+  c.warps = w->lists + w->nh + w->nc;
+  c.smalls = w->lists + w->nh + w->nc + w->nw;
+  c.hub_p = w->hub_p;
+  c.e = w->e;
+  c.x[0] = w->x0; c.x[1] = w->x1;
+  c.cb[0] = w->c0; c.cb[1] = w->c1;
+  c.part = w->part;
+  c.l1_part = w->l1_part;
+  c.dang_part = w->dang_part;
+  c.pull_blocks = g->blocks;
+  c.st = w->st;
+  c.args = w->args;
+  c.h_while = hw;
+  c.use_graph = use_graph ? 1u : 0u;
+  return c;
+}
+
+// One-time setup per graph and parameters: bins, hub prefix, buffers.
+static alb_status pr_setup(alb_graph g, cudaStream_t s) {
+  if (g->pr && g->pr->ready) return ALB_OK;
+  if (!g->pr) g->pr = new (std::nothrow) PrWs();
+  PrWs* w = g->pr;
+  if (!w) return ALB_ERR_OOM;
+  const uint32_t n = g->n;
+  const size_t nb = sizeof(float) * (size_t)n;
+  const uint32_t nblk = (n + kPartChunk - 1) / kPartChunk;
+  ALB_CUDA_TRY(cudaMalloc((void**)&w->lists, sizeof(uint32_t) * (size_t)n));
+  ALB_CUDA_TRY(cudaMalloc((void**)&w->cnt, sizeof(uint32_t) * (5 * (size_t)nblk + 5)));
+  ALB_CUDA_TRY(cudaMalloc((void**)&w->x0, nb));
+  ALB_CUDA_TRY(cudaMalloc((void**)&w->x1, nb));
+  ALB_CUDA_TRY(cudaMalloc((void**)&w->c0, nb));
+  ALB_CUDA_TRY(cudaMalloc((void**)&w->c1, nb));
+  ALB_CUDA_TRY(cudaMalloc((void**)&w->st, sizeof(PrState)));
+  ALB_CUDA_TRY(cudaMalloc((void**)&w->args, sizeof(PrArgs)));
+  ALB_CUDA_TRY(cudaMallocHost((void**)&w->h_st, sizeof(PrState)));
+  const uint32_t t = g->threshold, wmin = g->params.twc_warp_min, cmin = g->params.twc_cta_min;
+  uint32_t* totals = w->cnt + 5 * (size_t)nblk;
+  k_pr_count<<<nblk, kBlock, 0, s>>>(g->off, n, t, wmin, cmin, w->cnt);
+  k_pr_scan_counts<<<1, 32, 0, s>>>(w->cnt, nblk, totals);
+  uint32_t h[5];
+  ALB_CUDA_TRY(cudaMemcpyAsync(h, totals, sizeof(h), cudaMemcpyDeviceToHost, s));
+  ALB_CUDA_TRY(cudaStreamSynchronize(s));
+  w->nh = h[0]; w->nc = h[1]; w->nw = h[2]; w->ns = h[3]; w->zero_deg = h[4];
+  k_pr_scatter<<<nblk, kBlock, 0, s>>>(g->off, n, t, wmin, cmin, w->cnt, w->lists, w->nh, w->nc, w->nw);
+  ALB_CUDA_TRY(cudaMalloc((void**)&w->hub_p, sizeof(uint32_t) * ((size_t)w->nh + 1)));
+  k_pr_hub_prefix<<<1, kBlock, 0, s>>>(g->off, w->lists, w->nh, w->hub_p);
+  ALB_CUDA_TRY(cudaMemcpyAsync(&w->e, w->hub_p + w->nh, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  ALB_CUDA_TRY(cudaStreamSynchronize(s));
+  const size_t slots = (size_t)(w->e / 32u) + 1 + w->nh;
+  ALB_CUDA_TRY(cudaMalloc((void**)&w->part, sizeof(float) * slots));
+  ALB_CUDA_TRY(cudaMalloc((void**)&w->l1_part, sizeof(double) * ((size_t)g->blocks + w->nh)));
+  ALB_CUDA_TRY(cudaMalloc((void**)&w->dang_part, sizeof(float) * ((size_t)g->blocks + w->nh)));
+  ALB_CUDA_TRY(cudaGetLastError());
+  w->ready = true;
+  return ALB_OK;
+}
+
+static alb_status pr_add_kernel(cudaGraphNode_t* node, cudaGraph_t graph, const cudaGraphNode_t* dep,
+                                size_t ndep, void* fn, uint32_t grid, void** args) {
+  cudaKernelNodeParams kp{};
+  kp.func = fn;
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(kBlock);
+  kp.kernelParams = args;
+  ALB_CUDA_TRY(cudaGraphAddKernelNode(node, graph, dep, ndep, &kp));
+  return ALB_OK;
+}
+
+static alb_status pr_build_graph(alb_graph g) {
+  PrWs* w = g->pr;
+  cudaGraph_t G = nullptr;
+  ALB_CUDA_TRY(cudaGraphCreate(&G, 0));
+  auto fail = [&](alb_status s) { cudaGraphDestroy(G); return s; };
+  cudaGraphConditionalHandle hw;
+  if (cudaGraphConditionalHandleCreate(&hw, G, 1u, cudaGraphCondAssignDefault) != cudaSuccess)
+    return fail(ALB_ERR_CUDA);
+  PrCtx c = pr_ctx(g, true, hw);
+  float dang0 = (float)w->zero_deg / (float)g->n;
+  void* a_init[] = {&c, &dang0};
+  void* a_c[] = {&c};
+  cudaGraphNode_t n_init, n_while, n_pull, n_hub, n_fin, n_final, n_out;
+  alb_status rc;
+  if ((rc = pr_add_kernel(&n_init, G, nullptr, 0, (void*)k_pr_init, g->blocks, a_init)) != ALB_OK)
+    return fail(rc);
+  cudaGraphNodeParams wp{};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = hw;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  if (cudaGraphAddNode(&n_while, G, &n_init, nullptr, 1, &wp) != cudaSuccess) return fail(ALB_ERR_CUDA);
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  if ((rc = pr_add_kernel(&n_pull, body, nullptr, 0, (void*)k_pr_pull, g->blocks, a_c)) != ALB_OK)
+    return fail(rc);
+  cudaGraphNode_t last = n_pull;
+  if (w->nh) {
+    if ((rc = pr_add_kernel(&n_hub, body, &last, 1, (void*)k_pr_hub, g->lb_blocks, a_c)) != ALB_OK)
+      return fail(rc);
+    const uint32_t fin_blocks = (w->nh * 32 + kBlock - 1) / kBlock < g->blocks
+                                    ? (w->nh * 32 + kBlock - 1) / kBlock : g->blocks;
+    if ((rc = pr_add_kernel(&n_fin, body, &n_hub, 1, (void*)k_pr_hub_fin, fin_blocks ? fin_blocks : 1,
+                            a_c)) != ALB_OK)
+      return fail(rc);
+    last = n_fin;
+  }
+  if ((rc = pr_add_kernel(&n_final, body, &last, 1, (void*)k_pr_finalize, 1, a_c)) != ALB_OK)
+    return fail(rc);
+  if ((rc = pr_add_kernel(&n_out, G, &n_while, 1, (void*)k_pr_output, g->blocks, a_c)) != ALB_OK)
+    return fail(rc);
+  cudaGraphExec_t ex = nullptr;
+  if (cudaGraphInstantiate(&ex, G, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ALB_ERR_CUDA);
+  }
+  w->graph = G;
+  w->exec = ex;
+  return ALB_OK;
+}
+
+static alb_status pr_host_loop(alb_graph g, cudaStream_t s, uint32_t max_iter, double tol) {
+  PrWs* w = g->pr;
+  PrCtx c = pr_ctx(g, false, 0);
+  float dang0 = (float)w->zero_deg / (float)g->n;
+  k_pr_init<<<g->blocks, kBlock, 0, s>>>(c, dang0);
+  const uint32_t fin_blocks = w->nh ? ((w->nh * 32 + kBlock - 1) / kBlock < g->blocks
+                                           ? (w->nh * 32 + kBlock - 1) / kBlock : g->blocks) : 1;
+  const bool prof = g->params.profile != 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+  if (prof) { cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2); }
+  while (max_iter > 0) {
+    if (prof) cudaEventRecord(e0, s);
+    k_pr_pull<<<g->blocks, kBlock, 0, s>>>(c);
+    if (prof) cudaEventRecord(e1, s);
+    if (w->nh) {
+      k_pr_hub<<<g->lb_blocks, kBlock, 0, s>>>(c);
+      if (prof) cudaEventRecord(e2, s);
+      k_pr_hub_fin<<<fin_blocks ? fin_blocks : 1, kBlock, 0, s>>>(c);
+    }
+    k_pr_finalize<<<1, kBlock, 0, s>>>(c);
+    ALB_CUDA_TRY(cudaGetLastError());
+    ALB_CUDA_TRY(cudaMemcpyAsync(w->h_st, w->st, sizeof(PrState), cudaMemcpyDeviceToHost, s));
+    ALB_CUDA_TRY(cudaStreamSynchronize(s));
+    if (prof) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      g->stats.ms_inspect += ms; g->stats.n_inspect += 1;
+      if (w->nh) { cudaEventElapsedTime(&ms, e1, e2); g->stats.ms_lb += ms; g->stats.n_lb += 1; }
+    }
+    if (w->h_st->l1 < tol || w->h_st->iter >= max_iter) break;
+  }
+  if (prof) { cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2); }
+  k_pr_output<<<g->blocks, kBlock, 0, s>>>(c);
+  ALB_CUDA_TRY(cudaGetLastError());
+  return ALB_OK;
+}
+
+alb_status pr_stats(alb_graph g, alb_stats* out) {
+  PrWs* w = g->pr;
+  if (!w || !w->st) return ALB_OK;
+  ALB_CUDA_TRY(cudaMemcpy(w->h_st, w->st, sizeof(PrState), cudaMemcpyDeviceToHost));
+  out->rounds = w->h_st->iter;
+  out->pr_l1 = w->h_st->l1;
+  out->hub_rounds = w->nh ? w->h_st->iter : 0u;
+  out->max_hub_count = w->nh;
+  out->edges_lb = (uint64_t)w->e * w->h_st->iter;
+  out->edges_twc = (g->m - w->e) * (uint64_t)w->h_st->iter;
+  out->pushes = 0;
+  return ALB_OK;
+}
+
+}  // namespace alb
+
+using namespace alb;
+
+extern "C" alb_status alb_pagerank(alb_graph g, float damping, double tol, uint32_t max_iter,
+                                   float* hd_rank, double* hd_l1, uint32_t* hd_iters,
+                                   alb_stream stream) {
+  if (!g || !hd_rank || !(damping >= 0.0f && damping <= 1.0f) || !(tol >= 0.0)) return ALB_ERR_INVALID_ARG;
+  if (!(g->flags & ALB_SYMMETRIC)) return ALB_ERR_NOT_SYMMETRIC;
+  if (cudaSetDevice(g->device) != cudaSuccess) return ALB_ERR_CUDA;
+  g->stats.ms_inspect = g->stats.ms_lb = g->stats.ms_other = 0.0;
+  g->stats.n_inspect = g->stats.n_lb = g->stats.n_other = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  alb_status rc = pr_setup(g, s);
+  if (rc != ALB_OK) return rc;
+  PrWs* w = g->pr;
+  const bool dev_rank = is_device_ptr(hd_rank);
+  float* rank = hd_rank;
+  if (!dev_rank) {
+    if (!w->tmp_rank) ALB_CUDA_TRY(cudaMalloc((void**)&w->tmp_rank, sizeof(float) * (size_t)g->n));
+    rank = w->tmp_rank;
+  }
+  const bool dev_l1 = hd_l1 && is_device_ptr(hd_l1);
+  const bool dev_it = hd_iters && is_device_ptr(hd_iters);
+  PrArgs a{rank, damping, tol, max_iter, dev_l1 ? hd_l1 : nullptr, dev_it ? hd_iters : nullptr};
+  k_pr_set_args<<<1, 1, 0, s>>>(w->args, a);
+  ALB_CUDA_TRY(cudaMemsetAsync(w->st, 0, sizeof(PrState), s));
+  if (max_iter == 0) {
+    // no iteration: the output is the starting vector
+    PrCtx c = pr_ctx(g, false, 0);
+    k_pr_init<<<g->blocks, kBlock, 0, s>>>(c, (float)w->zero_deg / (float)g->n);
+    k_pr_output<<<g->blocks, kBlock, 0, s>>>(c);
+  } else if (g->params.exec_mode == 0) {
+    if (!w->exec) {
+      rc = pr_build_graph(g);
+      if (rc != ALB_OK) return rc;
+    }
+    ALB_CUDA_TRY(cudaGraphLaunch(w->exec, s));
+  } else {
+    rc = pr_host_loop(g, s, max_iter, tol);
+    if (rc != ALB_OK) return rc;
+  }
+  if (!dev_rank) ALB_CUDA_TRY(cudaMemcpyAsync(hd_rank, rank, sizeof(float) * g->n, cudaMemcpyDeviceToHost, s));
+  g->last_stream = s;
+  g->last_kind = 1;
+  if ((hd_l1 && !dev_l1) || (hd_iters && !dev_it)) {
+    ALB_CUDA_TRY(cudaStreamSynchronize(s));
+    ALB_CUDA_TRY(cudaMemcpy(w->h_st, w->st, sizeof(PrState), cudaMemcpyDeviceToHost));
+    if (hd_l1 && !dev_l1) *hd_l1 = w->h_st->l1;
+    if (hd_iters && !dev_it) *hd_iters = w->h_st->iter;
+  }
+  ALB_CUDA_TRY(cudaGetLastError());
+  return ALB_OK;
+}

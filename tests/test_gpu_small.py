@@ -1,0 +1,295 @@
+"""GPU parity on small graphs: every app through the C ABI against the CPU oracle.
+
+Integer apps must match bit for bit; PageRank within 1e-5 L1 of the FP64 oracle.
+Thresholds and TWC cut-offs are forced so that tiny graphs reach every bin and
+the LB kernel, in both the CUDA-graph and the host-loop execution modes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1911_09135_gb300 import graphgen as gg
+from tests import graphs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1911_09135_gb300 import alb  # noqa: E402
+
+PR_TOL = 1e-5
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a).astype(np.uint32).view(np.int32)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def make(g):
+    return alb.Graph(g.n, dev(g.offsets), dev(g.indices),
+                     dev(g.weights) if g.weights is not None else None, symmetric=g.symmetric)
+
+
+def run_all(G, g, src, k=3):
+    out = {}
+    o = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    G.bfs(src, o); out["bfs"] = host(o).copy()
+    if g.weights is not None:
+        G.sssp(src, o); out["sssp"] = host(o).copy()
+    if g.symmetric:
+        G.cc(o); out["cc"] = host(o).copy()
+        G.kcore(k, o); out["kcore"] = host(o).copy()
+    G.sync()
+    return out
+
+
+def oracle_all(g, src, k=3):
+    out = {"bfs": oracle.bfs(g.n, g.offsets, g.indices, src)}
+    if g.weights is not None:
+        out["sssp"] = oracle.sssp(g.n, g.offsets, g.indices, g.weights, src)
+    if g.symmetric:
+        out["cc"] = oracle.cc(g.n, g.offsets, g.indices)
+        out["kcore"] = oracle.kcore(g.n, g.offsets, g.indices, k)
+    return out
+
+
+SETTINGS = [
+    dict(hub_threshold=-1),
+    dict(hub_threshold=0),
+    dict(hub_threshold=1),
+    dict(hub_threshold=3, twc_warp_min=1, twc_cta_min=2),
+    dict(hub_threshold=8, twc_warp_min=2, twc_cta_min=4, distribution=1),
+    dict(hub_threshold=2, exec_mode=1),
+    dict(hub_threshold=1 << 40),
+    dict(hub_threshold=4, grid_blocks=3),
+]
+
+
+@pytest.mark.parametrize("g", graphs.all_small() + [graphs.directed_cycle_tail()],
+                         ids=lambda g: g.name)
+@pytest.mark.parametrize("setting", SETTINGS, ids=lambda s: ",".join(f"{k}={v}" for k, v in s.items()))
+def test_small_graphs_all_apps(g, setting):
+    G = make(g)
+    G.set_params(**setting)
+    for src in sorted({0, g.n - 1, g.n // 2}):
+        got = run_all(G, g, src)
+        ref = oracle_all(g, src)
+        for app in ref:
+            assert np.array_equal(got[app], ref[app]), (app, src)
+    G.close()
+
+
+@pytest.fixture(scope="module")
+def rmat13():
+    return gg.rmat(13, 16 << 13, 21, symmetrize=True, weighted=True, n_hubs=4, hub_degree=3000)
+
+
+@pytest.mark.parametrize("t", [0, 1, 31, 32, 33, 255, 256, 257, 2999, 3000, 3001, -1, 1 << 33])
+def test_threshold_sweep_identical_results(rmat13, t):
+    """Sec. 4.1: t = 0 (all huge) .. t > max degree (plain TWC) must give identical output."""
+    g = rmat13
+    src = g.max_degree_vertex()
+    G = make(g)
+    G.set_params(hub_threshold=t)
+    got = run_all(G, g, src, k=16)
+    ref = oracle_all(g, src, k=16)
+    for app in ref:
+        assert np.array_equal(got[app], ref[app]), app
+    st = G.stats()
+    if 0 <= t <= int(g.degrees().max()):
+        assert st["hub_rounds"] > 0  # kcore ran last; its LB kernel ran
+    G.close()
+
+
+@pytest.mark.parametrize("distribution", [0, 1])
+@pytest.mark.parametrize("exec_mode", [0, 1])
+def test_rmat_directed_bfs_and_modes(distribution, exec_mode):
+    g = gg.rmat16_directed()
+    G = make(g)
+    G.set_params(hub_threshold=2048, distribution=distribution, exec_mode=exec_mode)
+    o = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    for src in (0, 1, 12345):
+        G.bfs(src, o)
+        assert np.array_equal(host(o), oracle.bfs(g.n, g.offsets, g.indices, src))
+    G.close()
+
+
+@pytest.mark.parametrize("t", [-1, 0, 64, 1 << 33])
+@pytest.mark.parametrize("exec_mode", [0, 1])
+def test_pagerank_small(rmat13, t, exec_mode):
+    g = rmat13
+    G = make(g)
+    G.set_params(hub_threshold=t, exec_mode=exec_mode)
+    r = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    _, it, l1 = G.pagerank(0.85, 1e-6, 1000, r)
+    ref, it_ref, _ = oracle.pagerank(g.n, g.offsets, g.indices, 0.85, 1e-6, 1000,
+                                     assume_symmetric=True)
+    err = float(np.abs(r.cpu().numpy().astype(np.float64) - ref).sum())
+    assert err <= PR_TOL, err
+    assert abs(it - it_ref) <= 1 and l1 < 1e-6
+    G.close()
+
+
+def test_pagerank_deterministic_and_threshold_independent_within_tol(rmat13):
+    g = rmat13
+    G = make(g)
+    r1 = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    r2 = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    G.set_params(hub_threshold=64)
+    G.pagerank(0.85, 1e-6, 1000, r1)
+    G.pagerank(0.85, 1e-6, 1000, r2)
+    assert torch.equal(r1, r2)  # fixed reduction order: bit-reproducible
+    G.close()
+
+
+def test_pagerank_edge_cases():
+    for g in graphs.all_small():
+        G = make(g)
+        G.set_params(hub_threshold=2)
+        r = torch.empty(g.n, dtype=torch.float32, device="cuda")
+        G.pagerank(0.85, 1e-8, 500, r)
+        ref, _, _ = oracle.pagerank(g.n, g.offsets, g.indices, 0.85, 1e-8, 500, assume_symmetric=True)
+        assert float(np.abs(r.cpu().numpy() - ref).sum()) <= PR_TOL, g.name
+        # max_iter = 0 returns the starting vector
+        G.pagerank(0.85, 1e-8, 0, r)
+        assert np.allclose(r.cpu().numpy(), 1.0 / g.n)
+        G.close()
+
+
+def test_host_buffers_through_the_abi(rmat13):
+    g = rmat13
+    G = alb.Graph(g.n, g.offsets, g.indices, g.weights, symmetric=True)  # host CSR input
+    src = 5
+    lv = G.bfs(src)  # host output
+    assert np.array_equal(lv, oracle.bfs(g.n, g.offsets, g.indices, src))
+    d = G.sssp(src)
+    assert np.array_equal(d, oracle.sssp(g.n, g.offsets, g.indices, g.weights, src))
+    x, it, l1 = G.pagerank()
+    ref, _, _ = oracle.pagerank(g.n, g.offsets, g.indices, 0.85, 1e-6, 1000, assume_symmetric=True)
+    assert np.abs(x - ref).sum() <= PR_TOL
+    G.close()
+
+
+def test_inspect_matches_algorithm_1(rmat13):
+    g = rmat13
+    G = make(g)
+    rng = np.random.default_rng(1)
+    wl = rng.permutation(g.n)[:5000].astype(np.uint32)
+    for t in (0, 1, 32, 100, 1000, 1 << 33):
+        G.set_params(hub_threshold=t)
+        work, prefix, bins, counts = G.inspect(wl)
+        ow, op, ob, oc = oracle.inspect(g.n, g.offsets, wl, min(t, 0xFFFFFFFF))
+        assert np.array_equal(bins, ob) and np.array_equal(counts, oc)
+        # the huge set is unique; its order is the device's append order
+        assert np.array_equal(np.sort(work), np.sort(ow))
+        deg = g.degrees().astype(np.uint64)
+        assert np.array_equal(prefix.astype(np.uint64),
+                              np.concatenate([[0], np.cumsum(deg[work])]).astype(np.uint64))
+    G.close()
+
+
+@pytest.mark.parametrize("distribution", [0, 1])
+@pytest.mark.parametrize("grid", [0, 5])
+def test_lb_kernel_assignment_is_algorithm_2(rmat13, distribution, grid):
+    """The LB kernel itself deals position k to the thread Algorithm 2 names."""
+    g = rmat13
+    G = make(g)
+    G.set_params(hub_threshold=200, distribution=distribution, grid_blocks=grid)
+    p = G.stats()["lb_threads"]
+    wl = np.arange(g.n, dtype=np.uint32)
+    work, prefix, _, _ = oracle.inspect(g.n, g.offsets, wl, 200)
+    src, dst, thr = G.lb_trace(work, prefix.astype(np.uint32))
+    e = int(prefix[-1])
+    policy = "cyclic" if distribution == 0 else "blocked"
+    exp_src = np.empty(e, dtype=np.uint32)
+    exp_dst = np.empty(e, dtype=np.uint32)
+    exp_thr = np.empty(e, dtype=np.uint32)
+    busy = min(p, e) if policy == "cyclic" else -(-e // -(-e // p))  # threads holding positions
+    for i in range(busy):
+        ks, ss, ds = oracle.lb_edges(g.offsets, g.indices, work, prefix, p, i, policy)
+        exp_src[ks.astype(np.int64)] = ss
+        exp_dst[ks.astype(np.int64)] = ds
+        exp_thr[ks.astype(np.int64)] = i
+    assert np.array_equal(src, exp_src)
+    assert np.array_equal(dst, exp_dst)
+    assert np.array_equal(thr, exp_thr)
+    G.close()
+
+
+def test_lb_trace_rejects_inconsistent_prefix(rmat13):
+    g = rmat13
+    G = make(g)
+    work = np.array([0, 1], dtype=np.uint32)
+    bad = np.array([0, 5, 10], dtype=np.uint32)
+    with pytest.raises(alb.AlbError):
+        G.lb_trace(work, bad)
+    G.close()
+
+
+def test_argument_and_capability_errors():
+    g = graphs.directed_cycle_tail()
+    G = make(g)
+    o = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    with pytest.raises(alb.AlbError) as e:
+        G.bfs(g.n, o)
+    assert e.value.code == 1
+    with pytest.raises(alb.AlbError) as e:
+        G.cc(o)
+    assert e.value.code == 6
+    with pytest.raises(alb.AlbError) as e:
+        G.kcore(2, o)
+    assert e.value.code == 6
+    G.close()
+    g2 = gg.from_edges(3, [(0, 1), (1, 2)], symmetrize=True)
+    G2 = make(g2)
+    with pytest.raises(alb.AlbError) as e:
+        G2.sssp(0, o)
+    assert e.value.code == 7
+    G2.close()
+    # an index >= n in the CSR is caught at creation
+    off = np.array([0, 1, 2], dtype=np.uint32)
+    idx = np.array([1, 7], dtype=np.uint32)
+    with pytest.raises(alb.AlbError) as e:
+        alb.Graph(2, off, idx)
+    assert e.value.code == 8
+    # offsets[n] != m
+    with pytest.raises(alb.AlbError) as e:
+        alb.alb_graph_create(2, 1, off, idx[:1])
+    assert e.value.code == 1
+
+
+def test_round_limit_reports_timeout():
+    g = graphs.path(9)
+    G = make(g)
+    G.set_params(max_rounds=3)
+    o = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    G.bfs(0, o)
+    with pytest.raises(alb.AlbError) as e:
+        G.sync()
+    assert e.value.code == 4
+    G.set_params(max_rounds=0)
+    G.bfs(0, o)
+    G.sync()
+    assert np.array_equal(host(o), oracle.bfs(g.n, g.offsets, g.indices, 0))
+    G.close()
+
+
+def test_batch_matches_single_source(rmat13):
+    g = rmat13
+    G = make(g)
+    srcs = np.array([0, 7, 100, 4095], dtype=np.uint32)
+    out = torch.empty(len(srcs) * g.n, dtype=torch.int32, device="cuda")
+    G.bfs_batch(torch.from_numpy(srcs.view(np.int32)).cuda(), out)
+    res = host(out).reshape(len(srcs), g.n)
+    for i, s in enumerate(srcs):
+        assert np.array_equal(res[i], oracle.bfs(g.n, g.offsets, g.indices, int(s)))
+    G.sssp_batch(srcs, out)
+    res = host(out).reshape(len(srcs), g.n)
+    for i, s in enumerate(srcs):
+        assert np.array_equal(res[i], oracle.sssp(g.n, g.offsets, g.indices, g.weights, int(s)))
+    G.close()
