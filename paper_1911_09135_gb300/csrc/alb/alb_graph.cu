@@ -178,7 +178,7 @@ alb_status alb_graph_create(uint32_t n, uint64_t m, const uint32_t* hd_offsets,
   g->n = n;
   g->m = m;
   g->flags = flags;
-  g->has_w = hd_weights != nullptr;
+  g->has_w = hd_weights != nullptr || m == 0;  // a graph without edges has nothing to weigh
   const size_t nb = sizeof(uint32_t) * (size_t)n;
   const size_t mb = sizeof(uint32_t) * (size_t)(m ? m : 1);
   cudaError_t e = cudaSuccess;
@@ -199,7 +199,7 @@ alb_status alb_graph_create(uint32_t n, uint64_t m, const uint32_t* hd_offsets,
   }
   e = cudaMemcpyAsync(g->off, hd_offsets, nb + sizeof(uint32_t), cudaMemcpyDefault, s);
   if (e == cudaSuccess && m) e = cudaMemcpyAsync(g->idx, hd_indices, sizeof(uint32_t) * m, cudaMemcpyDefault, s);
-  if (e == cudaSuccess && g->has_w && m)
+  if (e == cudaSuccess && hd_weights && m)
     e = cudaMemcpyAsync(g->w, hd_weights, sizeof(uint32_t) * m, cudaMemcpyDefault, s);
   ScanOut* d_scan = nullptr;
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_scan, sizeof(ScanOut), s);

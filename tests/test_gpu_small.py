@@ -100,9 +100,12 @@ def test_threshold_sweep_identical_results(rmat13, t):
     ref = oracle_all(g, src, k=16)
     for app in ref:
         assert np.array_equal(got[app], ref[app]), app
+    o = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    G.bfs(src, o)
     st = G.stats()
-    if 0 <= t <= int(g.degrees().max()):
-        assert st["hub_rounds"] > 0  # kcore ran last; its LB kernel ran
+    # the source is the max-degree vertex: it is huge whenever t <= max degree
+    assert (st["hub_rounds"] > 0) == (0 <= t <= int(g.degrees().max()))
+    assert st["edges_twc"] + st["edges_lb"] == int(g.degrees()[host(o) != 0xFFFFFFFF].sum())
     G.close()
 
 
