@@ -58,7 +58,12 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["alb", "reference"], default="alb")
-    ap.add_argument("--workload", choices=["rmat24-hubs", "rmat22", "rmat16"], default="rmat24-hubs")
+    ap.add_argument("--workload", choices=["rmat24-hubs", "rmat22-hubs", "rmat22", "rmat16"],
+                    default="rmat24-hubs")
+    ap.add_argument("--apps", default="", help="comma list restricting the workload's apps")
+    ap.add_argument("--exec-mode", choices=["graph", "host"], default="graph",
+                    help="graph: device-side round loop (default); host: one launch per kernel "
+                         "(ncu cannot profile kernels inside graphs with conditional nodes)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-roofline", action="store_true")
@@ -72,6 +77,11 @@ def workload(name):
         g = gg.rmat24_hubs_sym()
         desc = ("RMAT(a=.57,b=.19,c=.19) scale 24, edge factor 16, seed 3, + 16 hubs x 2^22 "
                 "uniform targets, symmetrised, dedup, weights U[1,100]")
+        apps = APPS
+    elif name == "rmat22-hubs":
+        g = gg.scaled_hub_graph(22)
+        desc = ("RMAT scale 22, edge factor 16, seed 3, + 16 hubs x 2^20 uniform targets, "
+                "symmetrised, dedup, weights U[1,100] (small member of the severe-imbalance family)")
         apps = APPS
     elif name == "rmat22":
         g = gg.rmat22_sym()
@@ -293,7 +303,11 @@ def gpu_arm(args, dist):
     torch.cuda.set_device(dist.local)
     alb.load()
     g, desc, apps = workload(args.workload)
+    if args.apps:
+        apps = tuple(a for a in args.apps.split(",") if a in apps)
     step = GpuStep(g, apps, alb, torch)
+    if args.exec_mode == "host":
+        step.G.set_params(exec_mode=1)
     units, launches, cal_stats = step.calibrate()
     units_step = sum(units.values())
     stream = torch.cuda.current_stream()
@@ -370,7 +384,7 @@ def gpu_arm(args, dist):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32 (integer apps), f32 (pagerank)", "data": "synthetic",
         "config": {"workload": f"{g.name}: {desc}", "n": g.n, "m": g.m, "apps": list(apps),
-                   "source": int(step.src), "kcore_k": KCORE_K,
+                   "exec_mode": args.exec_mode, "source": int(step.src), "kcore_k": KCORE_K,
                    "pagerank": {"d": PR_D, "tol": PR_TOL},
                    "hub_threshold": cal_stats[apps[0]]["hub_threshold"],
                    "lb_threads": cal_stats[apps[0]]["lb_threads"],
