@@ -192,6 +192,33 @@ alb_status alb_lb_trace(alb_graph g, const uint32_t* hd_work, const uint32_t* hd
  * threads launched = SMs x resident threads per SM (80 x 2048 = 163840 on V100). */
 uint32_t alb_threshold_rule(uint32_t num_sms, uint32_t threads_per_sm);
 
+/* ------------------------------------------------------ allocation-free */
+
+/* Largest graph alb_bfs_noalloc accepts. */
+#define ALB_NOALLOC_MAX_VERTICES (1u << 20)
+
+/* BFS for callers that cannot allocate device memory: for instance code running
+ * while another stream captures a CUDA graph, a service whose device memory is
+ * all owned by another allocator, or a latency-bound loop that must not block
+ * the device in cudaMalloc/cudaFree. The paper has no counterpart: this is a
+ * packaging of the same bfs path (same kernels and results as alb_bfs with
+ * default parameters). It needs no alb_graph and never allocates: its scratch
+ * (frontiers, huge worklist and prefix sums, round state; about 16.8 MB) is one
+ * fixed array in the library's device image, held on every GPU that loads the
+ * library until the process exits.
+ *   n <= ALB_NOALLOC_MAX_VERTICES, else ALB_ERR_INVALID_ARG (nothing enqueued);
+ *   d_offsets[n+1], d_indices[m], d_levels[n] must be device memory.
+ * The CSR is checked on the device first (ALB_ERR_INVALID_ARG if offsets[0] != 0
+ * or offsets[n] != m, ALB_ERR_DEVICE if an index is >= n). The call synchronises
+ * `stream` once per round and returns after d_levels is complete.
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture begins. Every call on a device shares
+ * the one array and overwrites it, so calls whose work overlaps on the GPU
+ * (other threads, other streams) race and must be serialised by the caller. */
+alb_status alb_bfs_noalloc(uint32_t n, uint64_t m, const uint32_t* d_offsets,
+                           const uint32_t* d_indices, uint32_t src, uint32_t* d_levels,
+                           alb_stream stream);
+
 /* Wait for the handle's last call and return any latched device error. */
 alb_status alb_sync(alb_graph g);
 

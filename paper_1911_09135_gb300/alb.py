@@ -32,7 +32,7 @@ EXPORTS = [
     "alb_graph_create", "alb_graph_destroy", "alb_default_params", "alb_set_params",
     "alb_get_params", "alb_bfs", "alb_sssp", "alb_cc", "alb_pagerank", "alb_kcore",
     "alb_bfs_batch", "alb_sssp_batch", "alb_inspect", "alb_lb_trace", "alb_threshold_rule",
-    "alb_sync", "alb_get_stats", "alb_status_str", "alb_version",
+    "alb_sync", "alb_get_stats", "alb_status_str", "alb_version", "alb_bfs_noalloc",
 ]
 
 
@@ -114,6 +114,7 @@ def load(build_if_missing: bool = False):
         "alb_get_stats": ([_P, ctypes.POINTER(alb_stats)], S),
         "alb_status_str": ([S], ctypes.c_char_p),
         "alb_version": ([], _U32),
+        "alb_bfs_noalloc": ([_U32, ctypes.c_uint64, _P, _P, _U32, _P, _P], S),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -269,6 +270,15 @@ def alb_status_str(code: int) -> str:
 
 def alb_version() -> int:
     return int(load().alb_version())
+
+
+ALB_NOALLOC_MAX_VERTICES = 1 << 20
+
+
+def alb_bfs_noalloc(n, m, offsets, indices, src, levels, stream=None) -> None:
+    """BFS that allocates nothing (see include/alb.h): CUDA tensors in and out."""
+    _check(load().alb_bfs_noalloc(n, m, _ptr(offsets), _ptr(indices), src, _ptr(levels),
+                                  _stream(stream)), "alb_bfs_noalloc")
 
 
 # ------------------------------------------------------------- convenience wrapper

@@ -765,3 +765,150 @@ alb_status launch_lb_trace(alb_graph g, const uint32_t* d_work, const uint32_t* 
 }
 
 }  // namespace alb
+
+// ------------------------------------------------ BFS without any allocation
+//
+// alb_bfs_noalloc serves callers that cannot allocate device memory: code that
+// runs while a CUDA graph is being captured on another stream, services whose
+// device memory is entirely owned by another pool (a framework's caching
+// allocator), and real-time loops where a cudaMalloc/cudaFree would block on
+// the whole device. It runs the same BFS kernels as alb_bfs, with every scratch
+// buffer (two frontiers, the huge worklist and its prefix sums, the round
+// state) carved from one fixed-size __device__ array that lives in the module
+// for as long as the library is loaded on a device.
+
+#include <mutex>
+
+namespace alb {
+
+constexpr uint32_t kNoAllocMaxVertices = 1u << 20;
+constexpr size_t kNoAllocVec = ((sizeof(uint32_t) * ((size_t)kNoAllocMaxVertices + 1) + 255) / 256) * 256;
+constexpr size_t kNoAllocBytes = 4 * kNoAllocVec + 3 * 256;
+
+// Shared by every call on a device: calls whose work overlaps on the GPU race on it.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+struct NoAllocCheck {
+  uint32_t bad;
+  uint32_t off0;
+  uint32_t offn;
+};
+
+// One pass over the caller's CSR, so the traversal kernels never index out of range.
+__global__ void k_noalloc_check(const uint32_t* off, const uint32_t* idx, uint32_t n, uint64_t m,
+                                NoAllocCheck* out) {
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint32_t bad = 0;
+  for (uint64_t v = tid; v < n; v += stride)
+    if (off[v + 1] < off[v]) bad = 1;
+  for (uint64_t e = tid; e < m; e += stride)
+    if (idx[e] >= n) bad = 1;
+  if (bad) atomicOr(&out->bad, 1u);
+  if (tid == 0) {
+    out->off0 = off[0];
+    out->offn = off[n];
+  }
+}
+
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static unsigned char* g_noalloc_base[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once per
+// device (host code cannot use the symbol itself: it names a host-side shadow).
+static alb_status noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return ALB_ERR_CUDA; }
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return ALB_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_base[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) { cudaGetLastError(); return ALB_ERR_CUDA; }
+    g_noalloc_base[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_noalloc_base[dev];
+  return ALB_OK;
+}
+
+}  // namespace alb
+
+extern "C" alb_status alb_bfs_noalloc(uint32_t n, uint64_t m, const uint32_t* d_offsets,
+                                      const uint32_t* d_indices, uint32_t src, uint32_t* d_levels,
+                                      alb_stream stream) {
+  using namespace alb;
+  if (n == 0 || n > kNoAllocMaxVertices) return ALB_ERR_INVALID_ARG;
+  if (m >= 0xFFFFFFFFull) return ALB_ERR_OVERFLOW;
+  if (!d_offsets || (m && !d_indices) || !d_levels || src >= n) return ALB_ERR_INVALID_ARG;
+  if (!is_device_ptr(d_offsets) || (m && !is_device_ptr(d_indices)) || !is_device_ptr(d_levels))
+    return ALB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char* base = nullptr;
+  alb_status rc = noalloc_scratch(&base);
+  if (rc != ALB_OK) return rc;
+  uint32_t* F0 = reinterpret_cast<uint32_t*>(base);
+  uint32_t* F1 = reinterpret_cast<uint32_t*>(base + kNoAllocVec);
+  uint32_t* hub_v = reinterpret_cast<uint32_t*>(base + 2 * kNoAllocVec);
+  uint32_t* hub_p = reinterpret_cast<uint32_t*>(base + 3 * kNoAllocVec);
+  RoundState* st = reinterpret_cast<RoundState*>(base + 4 * kNoAllocVec);
+  CallArgs* args = reinterpret_cast<CallArgs*>(base + 4 * kNoAllocVec + 256);
+  NoAllocCheck* chk = reinterpret_cast<NoAllocCheck*>(base + 4 * kNoAllocVec + 512);
+  static_assert(sizeof(RoundState) <= 256 && sizeof(CallArgs) <= 256, "scratch layout");
+
+  int dev = 0, sms = 0;
+  ALB_CUDA_TRY(cudaGetDevice(&dev));
+  ALB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  uint32_t occ_i = 1, occ_l = 1;
+  occupancy(&occ_i, &occ_l);
+  const uint32_t blocks = (uint32_t)sms * occ_i, lb_blocks = (uint32_t)sms * occ_l;
+
+  // validate the caller's CSR (this call's contents of the shared scratch start here)
+  NoAllocCheck h{};
+  ALB_CUDA_TRY(cudaMemsetAsync(chk, 0, sizeof(NoAllocCheck), s));
+  k_noalloc_check<<<(unsigned)sms * 4, 256, 0, s>>>(d_offsets, d_indices, n, m, chk);
+  ALB_CUDA_TRY(cudaGetLastError());
+  ALB_CUDA_TRY(cudaMemcpyAsync(&h, chk, sizeof(h), cudaMemcpyDeviceToHost, s));
+  ALB_CUDA_TRY(cudaStreamSynchronize(s));
+  if (h.off0 != 0u || (uint64_t)h.offn != m) return ALB_ERR_INVALID_ARG;
+  if (h.bad) return ALB_ERR_DEVICE;
+
+  TravCtx c{};
+  c.off = d_offsets;
+  c.idx = d_indices;
+  c.w = nullptr;
+  c.n = n;
+  c.threshold = lb_blocks * (uint32_t)kBlock;  // the paper's rule: threads of the LB kernel
+  c.warp_min = 32u;
+  c.cta_min = (uint32_t)kBlock;
+  c.distribution = 0u;
+  c.max_rounds = n + 1u;
+  c.use_graph = 0u;
+  c.F0 = F0;
+  c.F1 = F1;
+  c.hub_v = hub_v;
+  c.hub_p = hub_p;
+  c.stamp = nullptr;  // bfs needs no round stamps
+  c.st = st;
+  c.args = args;
+
+  CallArgs ca{d_levels, src, 0u, nullptr, nullptr, nullptr};
+  k_set_args<<<1, 1, 0, s>>>(args, ca);
+  ALB_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(RoundState), s));  // counters must start at zero
+  void* kargs[] = {&c};
+  ALB_CUDA_TRY(cudaLaunchKernel((void*)k_init<APP_BFS>, dim3(blocks), dim3(kBlock), kargs, 0, s));
+  RoundState hs{};
+  for (;;) {
+    ALB_CUDA_TRY(cudaLaunchKernel((void*)k_inspect<BfsOp>, dim3(blocks), dim3(kBlock), kargs, 0, s));
+    ALB_CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    ALB_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hs.hub_packed >> 32) {
+      ALB_CUDA_TRY(cudaLaunchKernel((void*)k_lb<BfsOp, false>, dim3(lb_blocks), dim3(kBlock), kargs, 0, s));
+      ALB_CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+      ALB_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    if (hs.status & ST_ERR_ROUNDS) return ALB_ERR_TIMEOUT;
+    if (hs.fcount[hs.round & 1u] == 0u) break;
+  }
+  return ALB_OK;
+}
