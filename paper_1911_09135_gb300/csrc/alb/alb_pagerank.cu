@@ -14,12 +14,15 @@
 // Recurrence (N = n, deg = out-degree, D_t = mass on degree-0 vertices):
 //   x_0 = 1/N,  x_{t+1}[v] = (1-d)/N + d * (sum_{u->v} x_t[u]/deg(u) + D_t/N).
 #include <new>
+#include <vector>
 
 #include "alb_device.cuh"
 
 namespace alb {
 
 constexpr uint32_t kPartChunk = 4096;  // vertices per CTA in the stable partition
+constexpr uint32_t kFinTask = 4096;    // hub partial slots per first-level reduction task
+constexpr uint32_t kFinDirect = 256;   // shorter slot runs are summed by the hub's own warp
 
 struct PrState {
   uint32_t iter;
@@ -55,6 +58,11 @@ struct PrCtx {
   double* l1_part;             // per pull-CTA, then per hub
   float* dang_part;
   uint32_t pull_blocks;
+  uint32_t ntask;              // hub-sum tasks (runs of <= kFinTask slots of one hub)
+  const uint32_t* task_start;
+  const uint32_t* task_len;
+  const uint32_t* hub_t0;      // tasks of hub j: [hub_t0[j], hub_t0[j+1])
+  float* part2;
   PrState* st;
   const PrArgs* args;
   cudaGraphConditionalHandle h_while;
@@ -76,6 +84,11 @@ struct PrWs {
   float* part = nullptr;
   double* l1_part = nullptr;
   float* dang_part = nullptr;
+  uint32_t pull_blocks = 0, hub_blocks = 0, ntask = 0;
+  uint32_t* task_start = nullptr;
+  uint32_t* task_len = nullptr;
+  uint32_t* hub_t0 = nullptr;
+  float* part2 = nullptr;
   alb::PrState* st = nullptr;
   alb::PrState* h_st = nullptr;
   alb::PrArgs* args = nullptr;
@@ -226,57 +239,94 @@ __device__ __forceinline__ void block_reduce_store(double l1, float dang, double
   }
 }
 
-// CTA, warp and thread bins (static assignment, fixed reduction order).
+// Sum of x/deg over the in-edges idx[b + o], idx[b + o + S], ... (< deg) of one vertex, in that
+// order. U index loads are issued before their U dependent gathers, so a thread keeps U requests
+// in flight; the index stream is read once (evict-first), the gathers go through the read-only path.
+template <int U>
+__device__ __forceinline__ float strided_sum(const uint32_t* __restrict__ idx, const float* __restrict__ cb,
+                                             uint32_t b, uint32_t deg, uint32_t o, uint32_t S) {
+  float s = 0.0f;
+  for (uint32_t e0 = o; e0 < deg; e0 += S * U) {
+    uint32_t id[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t e = e0 + (uint32_t)u * S;
+      id[u] = e < deg ? __ldcs(idx + b + e) : kInf;
+    }
+    float v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = id[u] != kInf ? __ldg(cb + id[u]) : 0.0f;
+#pragma unroll
+    for (int u = 0; u < U; ++u) s += v[u];
+  }
+  return s;
+}
+
+constexpr uint32_t kCtaBatch = 32;  // CTA-bin vertices per barrier
+
+// CTA, warp and thread bins. Static assignment (entry j of a bin always goes to the same
+// CTA / warp / thread), fixed reduction order, so sums and partials are reproducible.
 __global__ void __launch_bounds__(kBlock) k_pr_pull(PrCtx c) {
-  __shared__ float s_red[kWarps];
+  __shared__ float s_part[kCtaBatch][kWarps + 1];
   const PrArgs* pa = c.args;
   const float d = pa->damping;
   const uint32_t par = c.st->iter & 1u;
   const float N = (float)c.n;
   const float base = (1.0f - d) / N + d * (c.st->dangling / N);
-  const float* cb = c.cb[par];
+  const float* __restrict__ cb = c.cb[par];
+  const uint32_t* __restrict__ idx = c.idx;
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   double l1 = 0.0;
   float dang = 0.0f;
-  // CTA bin: the CTA sums one vertex's in-edges
-  for (uint32_t j = blockIdx.x; j < c.nc; j += gridDim.x) {
-    const uint32_t v = c.ctas[j];
-    const uint32_t b = c.off[v], deg = c.off[v + 1] - b;
-    float s = 0.0f;
-    for (uint32_t e = tid; e < deg; e += kBlock) s += cb[__ldg(c.idx + b + e)];
-    s = warp_sum(s);
-    if (lane == 0) s_red[warp] = s;
+  // CTA bin: entries blockIdx.x + i * gridDim.x; every warp sums a strided slice of the
+  // vertex's edges, the 8 warp sums of a batch of 32 vertices are combined after one barrier.
+  const uint32_t G = gridDim.x;
+  for (uint32_t q = blockIdx.x; q < c.nc; q += G * kCtaBatch) {
+#pragma unroll 1
+    for (uint32_t i = 0; i < kCtaBatch; ++i) {
+      const uint32_t j = q + i * G;
+      if (j >= c.nc) break;  // CTA-uniform
+      const uint32_t v = c.ctas[j];
+      const uint32_t b = c.off[v], deg = c.off[v + 1] - b;
+      float sv = strided_sum<4>(idx, cb, b, deg, tid, kBlock);
+      sv = warp_sum(sv);
+      if (lane == 0) s_part[i][warp] = sv;
+    }
     __syncthreads();
-    if (tid == 0) {
-      float t = 0.0f;
-      for (int w = 0; w < kWarps; ++w) t += s_red[w];
-      pr_update(c, v, deg, t, base, d, par, l1, dang);
+    if (tid < kCtaBatch) {
+      const uint32_t j = q + tid * G;
+      if (j < c.nc) {
+        float t = 0.0f;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) t += s_part[tid][w];
+        const uint32_t v = c.ctas[j];
+        pr_update(c, v, c.off[v + 1] - c.off[v], t, base, d, par, l1, dang);
+      }
     }
     __syncthreads();
   }
-  // warp bin
+  // warp bin: one warp per vertex
   const uint32_t gw = blockIdx.x * kWarps + warp, nwarps = gridDim.x * kWarps;
   for (uint32_t j = gw; j < c.nw; j += nwarps) {
     const uint32_t v = c.warps[j];
     const uint32_t b = c.off[v], deg = c.off[v + 1] - b;
-    float s = 0.0f;
-    for (uint32_t e = lane; e < deg; e += 32) s += cb[__ldg(c.idx + b + e)];
-    s = warp_sum(s);
-    if (lane == 0) pr_update(c, v, deg, s, base, d, par, l1, dang);
+    float sv = warp_sum(strided_sum<4>(idx, cb, b, deg, lane, 32));
+    if (lane == 0) pr_update(c, v, deg, sv, base, d, par, l1, dang);
   }
-  // thread bin
+  // thread bin: one thread per vertex, its edges in order, 8 loads in flight
   const uint32_t gt = blockIdx.x * kBlock + tid, nthreads = gridDim.x * kBlock;
   for (uint32_t j = gt; j < c.ns; j += nthreads) {
     const uint32_t v = c.smalls[j];
     const uint32_t b = c.off[v], deg = c.off[v + 1] - b;
-    float s = 0.0f;
-    for (uint32_t e = 0; e < deg; ++e) s += cb[__ldg(c.idx + b + e)];
-    pr_update(c, v, deg, s, base, d, par, l1, dang);
+    pr_update(c, v, deg, strided_sum<8>(idx, cb, b, deg, 0, 1), base, d, par, l1, dang);
   }
   block_reduce_store<kBlock>(l1, dang, c.l1_part + blockIdx.x, c.dang_part + blockIdx.x);
 }
 
-// Huge vertices, cyclic over all threads: per-warp segmented sums into slots.
+// Huge vertices, cyclic over all threads (Algorithm 2): thread gt takes positions gt, gt + p, ...
+// four per iteration. Each warp covers 32 consecutive positions; their values are reduced per
+// source vertex (segmented scan) and each segment's sum is written to the slot
+// (position / 32) + source index, unique per (chunk, vertex) pair.
 __global__ void __launch_bounds__(kBlock) k_pr_hub(PrCtx c) {
   __shared__ uint32_t s_p[kHubSmem];
   __shared__ uint32_t s_base[kHubSmem];
@@ -291,36 +341,67 @@ __global__ void __launch_bounds__(kBlock) k_pr_hub(PrCtx c) {
   }
   __syncthreads();
   const uint32_t* P = staged ? s_p : c.hub_p;
-  const float* cb = c.cb[c.st->iter & 1u];
+  const float* __restrict__ cb = c.cb[c.st->iter & 1u];
   const uint32_t lane = threadIdx.x & 31u;
   const uint64_t p = (uint64_t)gridDim.x * kBlock;
   const uint64_t gt = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
+  constexpr int U = 4;
   uint32_t j = 0u;
-  for (uint64_t k0 = gt - lane; k0 < e; k0 += p) {  // warp-uniform; lane takes k0 + lane
-    const uint64_t k = k0 + lane;
-    const bool ok = k < e;
-    float val = 0.0f;
-    uint32_t jj = kInf;
-    if (ok) {
-      j = upper_search(P, j, nh, (uint32_t)k);
-      jj = j;
-      const uint32_t base = staged ? s_base[j] : c.off[c.hubs[j]] - c.hub_p[j];
-      val = cb[__ldg(c.idx + (uint32_t)k + base)];
-    }
-    // segmented inclusive scan by hub index (positions are consecutive in the warp)
+  for (uint64_t k0 = gt - lane; k0 < e; k0 += p * U) {  // warp-uniform
+    uint32_t jj[U], id[U];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const float y = __shfl_up_sync(kFull, val, o);
-      const uint32_t jy = __shfl_up_sync(kFull, jj, o);
-      if (lane >= (uint32_t)o && jy == jj) val += y;
+    for (int u = 0; u < U; ++u) {
+      const uint64_t k = k0 + (uint64_t)u * p + lane;
+      jj[u] = kInf;
+      id[u] = kInf;
+      if (k < e) {
+        j = upper_search(P, j, nh, (uint32_t)k);
+        jj[u] = j;
+        const uint32_t base = staged ? s_base[j] : c.off[c.hubs[j]] - c.hub_p[j];
+        id[u] = __ldcs(c.idx + (uint32_t)k + base);
+      }
     }
-    const uint32_t jn = __shfl_down_sync(kFull, jj, 1);
-    const bool tail = ok && (lane == 31 || jn != jj);
-    if (tail) c.part[(uint32_t)(k0 >> 5) + jj] = val;
+    float val[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) val[u] = id[u] != kInf ? __ldg(cb + id[u]) : 0.0f;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float y = __shfl_up_sync(kFull, val[u], o);
+        const uint32_t jy = __shfl_up_sync(kFull, jj[u], o);
+        if (lane >= (uint32_t)o && jy == jj[u]) val[u] += y;
+      }
+      const uint32_t jn = __shfl_down_sync(kFull, jj[u], 1);
+      const bool tail = jj[u] != kInf && (lane == 31 || jn != jj[u]);
+      if (tail) c.part[(uint32_t)((k0 + (uint64_t)u * p) >> 5) + jj[u]] = val[u];
+    }
   }
 }
 
-// One warp per huge vertex: sum its slots in chunk order, then update.
+// First level of the hub sums: one CTA per task (a run of at most kFinTask slots of one hub),
+// fixed-order sum into part2[task].
+__global__ void __launch_bounds__(kBlock) k_pr_hub_fin1(PrCtx c) {
+  __shared__ float s_red[kWarps];
+  for (uint32_t t = blockIdx.x; t < c.ntask; t += gridDim.x) {
+    const uint32_t s0 = c.task_start[t], len = c.task_len[t];
+    float s = 0.0f;
+    for (uint32_t i = threadIdx.x; i < len; i += kBlock) s += c.part[s0 + i];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31u) == 0) s_red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float a = 0.0f;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) a += s_red[w];
+      c.part2[t] = a;
+    }
+    __syncthreads();
+  }
+}
+
+// One warp per huge vertex: the sum of its tasks' partials (or, for a short slot run, of the
+// slots themselves) in a fixed order, then the update.
 __global__ void __launch_bounds__(kBlock) k_pr_hub_fin(PrCtx c) {
   const PrArgs* pa = c.args;
   const float d = pa->damping;
@@ -332,8 +413,11 @@ __global__ void __launch_bounds__(kBlock) k_pr_hub_fin(PrCtx c) {
   for (uint32_t j = gw; j < c.nh; j += nwarps) {
     const uint32_t v = c.hubs[j];
     const uint32_t p0 = c.hub_p[j], p1 = c.hub_p[j + 1];
+    const uint32_t t0 = c.hub_t0[j], t1 = c.hub_t0[j + 1];
     float s = 0.0f;
-    if (p1 > p0) {
+    if (t1 > t0) {
+      for (uint32_t t = t0 + lane; t < t1; t += 32) s += c.part2[t];
+    } else if (p1 > p0) {
       const uint32_t w0 = p0 >> 5, w1 = (p1 - 1) >> 5;
       for (uint32_t w = w0 + lane; w <= w1; w += 32) s += c.part[w + j];
     }
@@ -402,6 +486,7 @@ alb_status free_pagerank(alb_graph g) {
   cudaFree(w->lists); cudaFree(w->hub_p); cudaFree(w->cnt);
   cudaFree(w->x0); cudaFree(w->x1); cudaFree(w->c0); cudaFree(w->c1);
   cudaFree(w->part); cudaFree(w->l1_part); cudaFree(w->dang_part);
+  cudaFree(w->task_start); cudaFree(w->task_len); cudaFree(w->hub_t0); cudaFree(w->part2);
   cudaFree(w->st); cudaFree(w->args); cudaFree(w->tmp_rank);
   if (w->h_st) cudaFreeHost(w->h_st);
   cudaGetLastError();
@@ -428,7 +513,12 @@ static PrCtx pr_ctx(alb_graph g, bool use_graph, cudaGraphConditionalHandle hw) 
   c.part = w->part;
   c.l1_part = w->l1_part;
   c.dang_part = w->dang_part;
-  c.pull_blocks = g->blocks;
+  c.pull_blocks = w->pull_blocks;
+  c.ntask = w->ntask;
+  c.task_start = w->task_start;
+  c.task_len = w->task_len;
+  c.hub_t0 = w->hub_t0;
+  c.part2 = w->part2;
   c.st = w->st;
   c.args = w->args;
   c.h_while = hw;
@@ -469,11 +559,54 @@ static alb_status pr_setup(alb_graph g, cudaStream_t s) {
   ALB_CUDA_TRY(cudaStreamSynchronize(s));
   const size_t slots = (size_t)(w->e / 32u) + 1 + w->nh;
   ALB_CUDA_TRY(cudaMalloc((void**)&w->part, sizeof(float) * slots));
-  ALB_CUDA_TRY(cudaMalloc((void**)&w->l1_part, sizeof(double) * ((size_t)g->blocks + w->nh)));
-  ALB_CUDA_TRY(cudaMalloc((void**)&w->dang_part, sizeof(float) * ((size_t)g->blocks + w->nh)));
+  // the pull kernel needs little shared memory: give the rest of the SM's on-chip memory to L1,
+  // which caches the popular entries of the x/deg gathers
+  ALB_CUDA_TRY(cudaFuncSetAttribute(k_pr_pull, cudaFuncAttributePreferredSharedMemoryCarveout, 5));
+  // grids: every PageRank kernel is persistent, sized by its own residency
+  int occ = 0;
+  ALB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pr_pull, kBlock, 0));
+  w->pull_blocks = g->params.grid_blocks ? g->params.grid_blocks : (uint32_t)g->num_sms * (uint32_t)(occ > 0 ? occ : 1);
+  ALB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pr_hub, kBlock, 0));
+  w->hub_blocks = g->params.grid_blocks ? g->params.grid_blocks : (uint32_t)g->num_sms * (uint32_t)(occ > 0 ? occ : 1);
+  ALB_CUDA_TRY(cudaMalloc((void**)&w->l1_part, sizeof(double) * ((size_t)w->pull_blocks + w->nh)));
+  ALB_CUDA_TRY(cudaMalloc((void**)&w->dang_part, sizeof(float) * ((size_t)w->pull_blocks + w->nh)));
+  // hub-sum tasks: each hub's slot run [w0 + j, w1 + j] cut into pieces of <= kFinTask slots;
+  // runs of <= kFinDirect slots are summed directly by the hub's warp
+  {
+    std::vector<uint32_t> hp((size_t)w->nh + 1);
+    ALB_CUDA_TRY(cudaMemcpy(hp.data(), w->hub_p, sizeof(uint32_t) * hp.size(), cudaMemcpyDeviceToHost));
+    std::vector<uint32_t> ts, tl, t0((size_t)w->nh + 1, 0u);
+    for (uint32_t j = 0; j < w->nh; ++j) {
+      t0[j] = (uint32_t)ts.size();
+      if (hp[j + 1] <= hp[j]) continue;
+      const uint32_t w0 = hp[j] >> 5, w1 = (hp[j + 1] - 1) >> 5, L = w1 - w0 + 1;
+      if (L <= kFinDirect) continue;
+      for (uint32_t o = 0; o < L; o += kFinTask) {
+        ts.push_back(w0 + j + o);
+        tl.push_back(L - o < kFinTask ? L - o : kFinTask);
+      }
+    }
+    t0[w->nh] = (uint32_t)ts.size();
+    w->ntask = (uint32_t)ts.size();
+    ALB_CUDA_TRY(cudaMalloc((void**)&w->hub_t0, sizeof(uint32_t) * t0.size()));
+    ALB_CUDA_TRY(cudaMemcpy(w->hub_t0, t0.data(), sizeof(uint32_t) * t0.size(), cudaMemcpyHostToDevice));
+    const size_t nt = ts.size() ? ts.size() : 1;
+    ALB_CUDA_TRY(cudaMalloc((void**)&w->task_start, sizeof(uint32_t) * nt));
+    ALB_CUDA_TRY(cudaMalloc((void**)&w->task_len, sizeof(uint32_t) * nt));
+    ALB_CUDA_TRY(cudaMalloc((void**)&w->part2, sizeof(float) * nt));
+    if (!ts.empty()) {
+      ALB_CUDA_TRY(cudaMemcpy(w->task_start, ts.data(), sizeof(uint32_t) * ts.size(), cudaMemcpyHostToDevice));
+      ALB_CUDA_TRY(cudaMemcpy(w->task_len, tl.data(), sizeof(uint32_t) * tl.size(), cudaMemcpyHostToDevice));
+    }
+  }
   ALB_CUDA_TRY(cudaGetLastError());
   w->ready = true;
   return ALB_OK;
+}
+
+static uint32_t pr_fin_blocks(const PrWs* w) {
+  const uint32_t b = (w->nh * 32u + kBlock - 1) / kBlock;
+  return b == 0 ? 1u : (b < w->pull_blocks ? b : w->pull_blocks);
 }
 
 static alb_status pr_add_kernel(cudaGraphNode_t* node, cudaGraph_t graph, const cudaGraphNode_t* dep,
@@ -510,16 +643,21 @@ static alb_status pr_build_graph(alb_graph g) {
   wp.conditional.size = 1;
   if (cudaGraphAddNode(&n_while, G, &n_init, nullptr, 1, &wp) != cudaSuccess) return fail(ALB_ERR_CUDA);
   cudaGraph_t body = wp.conditional.phGraph_out[0];
-  if ((rc = pr_add_kernel(&n_pull, body, nullptr, 0, (void*)k_pr_pull, g->blocks, a_c)) != ALB_OK)
+  if ((rc = pr_add_kernel(&n_pull, body, nullptr, 0, (void*)k_pr_pull, w->pull_blocks, a_c)) != ALB_OK)
     return fail(rc);
   cudaGraphNode_t last = n_pull;
   if (w->nh) {
-    if ((rc = pr_add_kernel(&n_hub, body, &last, 1, (void*)k_pr_hub, g->lb_blocks, a_c)) != ALB_OK)
+    if ((rc = pr_add_kernel(&n_hub, body, &last, 1, (void*)k_pr_hub, w->hub_blocks, a_c)) != ALB_OK)
       return fail(rc);
-    const uint32_t fin_blocks = (w->nh * 32 + kBlock - 1) / kBlock < g->blocks
-                                    ? (w->nh * 32 + kBlock - 1) / kBlock : g->blocks;
-    if ((rc = pr_add_kernel(&n_fin, body, &n_hub, 1, (void*)k_pr_hub_fin, fin_blocks ? fin_blocks : 1,
-                            a_c)) != ALB_OK)
+    last = n_hub;
+    if (w->ntask) {
+      cudaGraphNode_t n_fin1;
+      const uint32_t b1 = w->ntask < w->pull_blocks ? w->ntask : w->pull_blocks;
+      if ((rc = pr_add_kernel(&n_fin1, body, &last, 1, (void*)k_pr_hub_fin1, b1, a_c)) != ALB_OK)
+        return fail(rc);
+      last = n_fin1;
+    }
+    if ((rc = pr_add_kernel(&n_fin, body, &last, 1, (void*)k_pr_hub_fin, pr_fin_blocks(w), a_c)) != ALB_OK)
       return fail(rc);
     last = n_fin;
   }
@@ -542,19 +680,18 @@ static alb_status pr_host_loop(alb_graph g, cudaStream_t s, uint32_t max_iter, d
   PrCtx c = pr_ctx(g, false, 0);
   float dang0 = (float)w->zero_deg / (float)g->n;
   k_pr_init<<<g->blocks, kBlock, 0, s>>>(c, dang0);
-  const uint32_t fin_blocks = w->nh ? ((w->nh * 32 + kBlock - 1) / kBlock < g->blocks
-                                           ? (w->nh * 32 + kBlock - 1) / kBlock : g->blocks) : 1;
   const bool prof = g->params.profile != 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
   if (prof) { cudaEventCreate(&e0); cudaEventCreate(&e1); cudaEventCreate(&e2); }
   while (max_iter > 0) {
     if (prof) cudaEventRecord(e0, s);
-    k_pr_pull<<<g->blocks, kBlock, 0, s>>>(c);
+    k_pr_pull<<<w->pull_blocks, kBlock, 0, s>>>(c);
     if (prof) cudaEventRecord(e1, s);
     if (w->nh) {
-      k_pr_hub<<<g->lb_blocks, kBlock, 0, s>>>(c);
+      k_pr_hub<<<w->hub_blocks, kBlock, 0, s>>>(c);
       if (prof) cudaEventRecord(e2, s);
-      k_pr_hub_fin<<<fin_blocks ? fin_blocks : 1, kBlock, 0, s>>>(c);
+      if (w->ntask) k_pr_hub_fin1<<<w->ntask < w->pull_blocks ? w->ntask : w->pull_blocks, kBlock, 0, s>>>(c);
+      k_pr_hub_fin<<<pr_fin_blocks(w), kBlock, 0, s>>>(c);
     }
     k_pr_finalize<<<1, kBlock, 0, s>>>(c);
     ALB_CUDA_TRY(cudaGetLastError());

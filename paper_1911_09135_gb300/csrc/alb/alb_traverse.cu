@@ -86,9 +86,9 @@ __device__ __forceinline__ void relax(const TravCtx& c, const OpArgs& a, const u
                                       uint32_t* ncount) {
   uint32_t dst[U], wt[U], cur[U];
 #pragma unroll
-  for (int u = 0; u < U; ++u) dst[u] = ok[u] ? __ldg(c.idx + e[u]) : 0u;
+  for (int u = 0; u < U; ++u) dst[u] = ok[u] ? __ldcs(c.idx + e[u]) : 0u;  // streamed once: evict-first
 #pragma unroll
-  for (int u = 0; u < U; ++u) wt[u] = (Op::kW && ok[u]) ? __ldg(c.w + e[u]) : 0u;
+  for (int u = 0; u < U; ++u) wt[u] = (Op::kW && ok[u]) ? __ldcs(c.w + e[u]) : 0u;
 #pragma unroll
   for (int u = 0; u < U; ++u) cur[u] = ok[u] ? a.lab[dst[u]] : 0u;
 #pragma unroll
