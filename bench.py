@@ -58,8 +58,10 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["alb", "reference"], default="alb")
-    ap.add_argument("--workload", choices=["rmat24-hubs", "rmat22-hubs", "rmat22", "rmat16"],
-                    default="rmat24-hubs")
+    ap.add_argument("--workload", choices=["rmat24-hubs", "rmat22-hubs", "rmat22", "rmat16",
+                                           "batch-sources", "batch-graphs"],
+                    default="rmat24-hubs",
+                    help="batch-*: batched vs one-query-at-a-time throughput (separate line)")
     ap.add_argument("--apps", default="", help="comma list restricting the workload's apps")
     ap.add_argument("--exec-mode", choices=["graph", "host"], default="graph",
                     help="graph: device-side round loop (default); host: one launch per kernel "
@@ -516,9 +518,104 @@ def reference_arm(args, dist):
     print(json.dumps(line), flush=True)
 
 
+def batch_arm(args, dist):
+    """Batched traversal throughput against the one-query-at-a-time plain path, same GPU.
+
+    batch-sources: 128 uniform random sources (seed 4) on rmat22-sym; plain = 128 alb_bfs /
+    alb_sssp calls, batched = one alb_bfs_batch / alb_sssp_batch call (groups of 32 sources).
+    batch-graphs: 512 RMAT graphs with samples log-uniform in [2^10, 2^22] (seed 4), source 0
+    of each; plain = one resident handle per graph, 512 calls; batched = one traversal of their
+    disjoint union from all 512 sources (alb_bfs_multi / alb_sssp_multi).
+    Outputs stay on the device in both paths; the graphs are resident before timing.
+    """
+    import torch
+    from paper_1911_09135_gb300 import alb, graphgen as gg
+
+    torch.cuda.set_device(dist.local)
+    alb.load()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    res = {}
+    if args.workload == "batch-sources":
+        g = gg.rmat22_sym()
+        rng = np.random.Generator(np.random.Philox(key=4))
+        srcs = rng.integers(0, g.n, size=128).astype(np.uint32)
+        d_srcs = dev(srcs)
+        G = alb.Graph(g.n, dev(g.offsets), dev(g.indices), dev(g.weights), symmetric=True)
+        out = torch.empty(128 * g.n, dtype=torch.int32, device="cuda")
+        n = g.n
+        for app, single, batch in (("bfs", alb.alb_bfs, alb.alb_bfs_batch),
+                                   ("sssp", alb.alb_sssp, alb.alb_sssp_batch)):
+            def plain():
+                for i, s in enumerate(srcs.tolist()):
+                    single(G.h, s, out[i * n:(i + 1) * n])
+            ms_plain = timed(plain, max(1, args.steps // 2))
+            ms_batch = timed(lambda: batch(G.h, d_srcs, 128, out), args.steps)
+            res[app] = {"queries": 128, "ms_plain": round(ms_plain, 3), "ms_batched": round(ms_batch, 3),
+                        "speedup": round(ms_plain / ms_batch, 2),
+                        "queries_per_s_batched": round(128 / (ms_batch * 1e-3), 1)}
+        G.close()
+        desc = "128 sources (seed 4) on rmat22-sym (scale 22, ef 16, seed 2, w in [1,100])"
+    else:
+        parts = gg.small_graphs(512, seed=4)
+        u, base = gg.disjoint_union(parts)
+        srcs = base[:-1].astype(np.uint32)
+        d_srcs = dev(srcs)
+        U = alb.Graph(u.n, dev(u.offsets), dev(u.indices), dev(u.weights), symmetric=True)
+        Gs = [alb.Graph(p.n, dev(p.offsets), dev(p.indices), dev(p.weights), symmetric=True)
+              for p in parts]
+        outs = [torch.empty(p.n, dtype=torch.int32, device="cuda") for p in parts]
+        out = torch.empty(u.n, dtype=torch.int32, device="cuda")
+        for app, single, multi in (("bfs", alb.alb_bfs, alb.alb_bfs_multi),
+                                   ("sssp", alb.alb_sssp, alb.alb_sssp_multi)):
+            def plain():
+                for G, o in zip(Gs, outs):
+                    single(G.h, 0, o)
+            ms_plain = timed(plain, max(1, args.steps // 2))
+            ms_batch = timed(lambda: multi(U.h, d_srcs, len(parts), out), args.steps)
+            res[app] = {"queries": len(parts), "ms_plain": round(ms_plain, 3),
+                        "ms_batched": round(ms_batch, 3), "speedup": round(ms_plain / ms_batch, 2),
+                        "queries_per_s_batched": round(len(parts) / (ms_batch * 1e-3), 1)}
+        for G in Gs:
+            G.close()
+        U.close()
+        desc = (f"512 RMAT graphs, samples log-uniform in [2^10, 2^22] (seed 4), symmetrised, "
+                f"w in [1,100]; union n={u.n} m={u.m}; source 0 of each")
+    q = sum(r["queries"] for r in res.values())
+    t = sum(r["ms_batched"] for r in res.values())
+    tp = sum(r["ms_plain"] for r in res.values())
+    line = {"metric": "batched throughput vs one-query-at-a-time plain path (bfs + sssp)",
+            "value": round(q / (t * 1e-3), 1), "unit": "queries/s", "n_gpus": dist.world,
+            "steps": args.steps, "higher_is_better": True, "speedup_vs_plain": round(tp / t, 2),
+            "config": {"workload": args.workload + ": " + desc}, "per_app": res}
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     dist = Dist()
+    if args.workload.startswith("batch-"):
+        import torch
+        dist.init("nccl" if torch.cuda.is_available() else "gloo")
+        try:
+            batch_arm(args, dist)
+        finally:
+            dist.done()
+        return
     if args.impl == "reference":
         if dist.world > 1 and dist.rank != 0:
             return

@@ -160,12 +160,25 @@ alb_status alb_kcore(alb_graph g, uint32_t k, uint32_t* hd_in_core, alb_stream s
 
 /* ---------------------------------------------------------------- batches */
 
-/* Many sources over one graph in one launch sequence: source s's result goes
- * to hd_out[s * n .. (s+1) * n) (source-major). Same semantics per source as
- * alb_bfs / alb_sssp. hd_srcs has k entries. */
+/* Many sources over one graph: source s's result goes to hd_out[s * n .. (s+1) * n)
+ * (source-major), identical per source to alb_bfs / alb_sssp. Sources run in groups of 32
+ * that share every CSR read: a frontier vertex carries the set of sources for which it is
+ * active and each expanded edge is relaxed for all of them (bit-parallel for bfs). The
+ * rounds use the same inspection, TWC and cyclic LB kernels (Algorithms 1 and 2). hd_srcs
+ * has k entries (repeats allowed); each must be < n, else ALB_ERR_INVALID_ARG. Workspace:
+ * 32 labels + a mask and two tagged masks per vertex (148 bytes x n), allocated on first use. */
 alb_status alb_bfs_batch(alb_graph g, const uint32_t* hd_srcs, uint32_t k, uint32_t* hd_out,
                          alb_stream stream);
 alb_status alb_sssp_batch(alb_graph g, const uint32_t* hd_srcs, uint32_t k, uint32_t* hd_out,
+                          alb_stream stream);
+
+/* One traversal from a set of sources at distance 0: hd_levels[v] (hd_dist[v]) = distance from
+ * the nearest of hd_srcs[0..k). On a graph that is the disjoint union of many graphs with one
+ * source in each, this computes every graph's own bfs (sssp) in one launch sequence, which is
+ * how many small graphs are batched. Each source must be < n. */
+alb_status alb_bfs_multi(alb_graph g, const uint32_t* hd_srcs, uint32_t k, uint32_t* hd_levels,
+                         alb_stream stream);
+alb_status alb_sssp_multi(alb_graph g, const uint32_t* hd_srcs, uint32_t k, uint32_t* hd_dist,
                           alb_stream stream);
 
 /* ------------------------------------------------------------ diagnostics */

@@ -33,6 +33,7 @@ ALB_SOURCES = [
 ALB_HEADERS = [
     "alb/alb_internal.cuh",
     "alb/alb_device.cuh",
+    "alb/alb_kernels.cuh",
 ]
 
 

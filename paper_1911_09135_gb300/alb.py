@@ -33,6 +33,7 @@ EXPORTS = [
     "alb_get_params", "alb_bfs", "alb_sssp", "alb_cc", "alb_pagerank", "alb_kcore",
     "alb_bfs_batch", "alb_sssp_batch", "alb_inspect", "alb_lb_trace", "alb_threshold_rule",
     "alb_sync", "alb_get_stats", "alb_status_str", "alb_version", "alb_bfs_noalloc",
+    "alb_bfs_multi", "alb_sssp_multi",
 ]
 
 
@@ -107,6 +108,8 @@ def load(build_if_missing: bool = False):
         "alb_kcore": ([_P, _U32, _P, _P], S),
         "alb_bfs_batch": ([_P, _P, _U32, _P, _P], S),
         "alb_sssp_batch": ([_P, _P, _U32, _P, _P], S),
+        "alb_bfs_multi": ([_P, _P, _U32, _P, _P], S),
+        "alb_sssp_multi": ([_P, _P, _U32, _P, _P], S),
         "alb_inspect": ([_P, _P, _U32, _P, _P, _P, _P, _P], S),
         "alb_lb_trace": ([_P, _P, _P, _U32, _P, _P, _P, _P], S),
         "alb_threshold_rule": ([_U32, _U32], _U32),
@@ -238,6 +241,14 @@ def alb_bfs_batch(g, srcs, k, out, stream=None) -> None:
 
 def alb_sssp_batch(g, srcs, k, out, stream=None) -> None:
     _check(load().alb_sssp_batch(g, _ptr(srcs), k, _ptr(out), _stream(stream)), "alb_sssp_batch")
+
+
+def alb_bfs_multi(g, srcs, k, levels, stream=None) -> None:
+    _check(load().alb_bfs_multi(g, _ptr(srcs), k, _ptr(levels), _stream(stream)), "alb_bfs_multi")
+
+
+def alb_sssp_multi(g, srcs, k, dist, stream=None) -> None:
+    _check(load().alb_sssp_multi(g, _ptr(srcs), k, _ptr(dist), _stream(stream)), "alb_sssp_multi")
 
 
 def alb_inspect(g, wl, nf, bins, work, prefix, counts, stream=None) -> None:
@@ -375,6 +386,18 @@ class Graph:
         k = _numel(srcs)
         out = self._out(out, np.uint32, k * self.n)
         alb_sssp_batch(self.h, srcs, k, out, stream)
+        return out
+
+    def bfs_multi(self, srcs, out=None, stream=None):
+        srcs = np.ascontiguousarray(srcs, dtype=np.uint32) if isinstance(srcs, (list, tuple, np.ndarray)) else srcs
+        out = self._out(out, np.uint32)
+        alb_bfs_multi(self.h, srcs, _numel(srcs), out, stream)
+        return out
+
+    def sssp_multi(self, srcs, out=None, stream=None):
+        srcs = np.ascontiguousarray(srcs, dtype=np.uint32) if isinstance(srcs, (list, tuple, np.ndarray)) else srcs
+        out = self._out(out, np.uint32)
+        alb_sssp_multi(self.h, srcs, _numel(srcs), out, stream)
         return out
 
     def inspect(self, worklist, stream=None):

@@ -1,56 +1,425 @@
-// Batched traversals: many sources over one graph.
-#include "alb_device.cuh"
+// Batched traversals.
+//
+// (1) Many sources on one graph (alb_bfs_batch, alb_sssp_batch). Sources run in groups of 32
+//     that share every read of the CSR: a frontier vertex carries the set of sources (a 32-bit
+//     mask) for which it is active, and the operator relaxes all of them along each edge it
+//     reads. Labels of a group are kept vertex-major (lab[v * 32 + s]), so the 32 labels of a
+//     vertex share one 128-byte line. The round kernels are the ALB kernels of every other
+//     traversal (inspection + TWC, the cyclic LB kernel, the device-side round loop); only the
+//     operator differs:
+//       bfs : bit-parallel (a `seen` mask per vertex; one atomicOr discovers up to 32 sources),
+//       sssp: per active source, the relaxation of Fig. 3 with atomicMin.
+//     The per-round masks live in two round-tagged 64-bit arrays ((round << 32) | mask), so a
+//     stale entry never needs clearing.
+// (2) Many small graphs (alb_bfs_multi, alb_sssp_multi): a traversal from a set of sources at
+//     distance 0. Run on the disjoint union of many graphs with one source in each, it computes
+//     every graph's own result in one launch sequence (components never interact).
+#include <cstdlib>
+#include <new>
+
+#include "alb_kernels.cuh"
+
+namespace alb {
+
+struct BatchAux {
+  uint32_t* lab;              // n x 32, vertex-major
+  uint32_t* seen;             // n: sources that reached v (bfs)
+  unsigned long long* act0;   // round-tagged masks, read in even rounds
+  unsigned long long* act1;   // ... odd rounds
+};
+
+__device__ __forceinline__ unsigned long long* act_of(const BatchAux* x, uint32_t round) {
+  return (round & 1u) ? x->act1 : x->act0;
+}
+
+// Sources for which v is active in round r (written during round r - 1 with tag r).
+__device__ __forceinline__ uint32_t act_mask(const BatchAux* x, uint32_t r, uint32_t v) {
+  const unsigned long long t = act_of(x, r)[v];
+  return ((uint32_t)(t >> 32) == r) ? (uint32_t)t : 0u;
+}
+
+// OR `bits` into the entry for round `tag`; true if the entry had no bit of that round before
+// (the caller then appends the vertex to the next frontier exactly once).
+__device__ __forceinline__ bool act_or(unsigned long long* p, uint32_t tag, uint32_t bits) {
+  unsigned long long old = *(volatile unsigned long long*)p, assumed;
+  do {
+    assumed = old;
+    const uint32_t ot = (uint32_t)(assumed >> 32), om = (uint32_t)assumed;
+    const uint32_t nm = (ot == tag) ? (om | bits) : bits;
+    if (ot == tag && nm == om) return false;
+    old = atomicCAS(p, assumed, ((unsigned long long)tag << 32) | nm);
+  } while (old != assumed);
+  // zero-initialised entries carry tag 0 with an empty mask
+  return (uint32_t)(assumed >> 32) != tag || (uint32_t)assumed == 0u;
+}
+
+// Multi-source bfs: sval is the vertex's source mask.
+struct MsBfsOp {
+  static constexpr bool kBatch = true;
+  static constexpr bool kW = false;
+  __device__ static uint32_t sval(const OpArgs& a, uint32_t v) {
+    return act_mask(static_cast<const BatchAux*>(a.aux), a.next - 1u, v);
+  }
+  __device__ static bool apply(const OpArgs& a, uint32_t M, uint32_t dst, uint32_t) {
+    const BatchAux* x = static_cast<const BatchAux*>(a.aux);
+    uint32_t nw = M & ~x->seen[dst];
+    if (!nw) return false;
+    nw &= ~atomicOr(x->seen + dst, nw);
+    if (!nw) return false;
+    uint32_t* row = x->lab + (size_t)dst * 32u;
+    for (uint32_t b = nw; b; b &= b - 1u) row[__ffs(b) - 1] = a.next;
+    return act_or(act_of(x, a.next) + dst, a.next, nw);
+  }
+};
+
+// Multi-source sssp: sval is the vertex id (its mask and labels are read per edge; they are
+// L1-resident while the vertex's edges are expanded). Per active source, the relaxation of
+// Fig. 3. The atomicMin does not wait for its old value: the destination is marked for the next
+// round whenever the pre-check saw an improvement, so the marked set contains every vertex
+// whose label dropped (possibly a few more, which only costs a redundant visit).
+struct MsSsspOp {
+  static constexpr bool kBatch = true;
+  static constexpr bool kW = true;
+  __device__ static uint32_t sval(const OpArgs&, uint32_t v) { return v; }
+  __device__ static bool apply(const OpArgs& a, uint32_t v, uint32_t dst, uint32_t w) {
+    const BatchAux* x = static_cast<const BatchAux*>(a.aux);
+    const uint32_t M = act_mask(x, a.next - 1u, v);
+    const uint32_t* ru = x->lab + (size_t)v * 32u;
+    uint32_t* rd = x->lab + (size_t)dst * 32u;
+    uint32_t nb = 0u;
+    for (uint32_t b = M; b; b &= b - 1u) {
+      const uint32_t s = __ffs(b) - 1;
+      const uint32_t du = ru[s];
+      if ((uint64_t)du + w < (uint64_t)rd[s]) {
+        atomicMin(rd + s, du + w);
+        nb |= 1u << s;
+      }
+    }
+    return nb && act_or(act_of(x, a.next) + dst, a.next, nb);
+  }
+};
+
+// ---- group kernels
+
+__global__ void __launch_bounds__(kBlock) k_batch_init(TravCtx c) {
+  const BatchAux* x = static_cast<const BatchAux*>(c.args->aux);
+  const uint64_t n = c.n;
+  for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < n * 32u;
+       i += (uint64_t)gridDim.x * kBlock)
+    x->lab[i] = kInf;
+  for (uint64_t v = (uint64_t)blockIdx.x * kBlock + threadIdx.x; v < n; v += (uint64_t)gridDim.x * kBlock) {
+    x->seen[v] = 0u;
+    x->act0[v] = 0ull;
+    x->act1[v] = 0ull;
+  }
+}
+
+__global__ void k_batch_seed(TravCtx c) {
+  const CallArgs* ca = c.args;
+  const BatchAux* x = static_cast<const BatchAux*>(ca->aux);
+  const uint32_t s = threadIdx.x;
+  if (s < ca->nsrc) {
+    const uint32_t v = ca->srcs[s], bit = 1u << s;
+    x->lab[(size_t)v * 32u + s] = 0u;
+    atomicOr(x->seen + v, bit);
+    if (act_or(x->act0 + v, 0u, bit)) c.F0[atomicAdd(&c.st->fcount[0], 1u)] = v;
+  }
+}
+
+// lab (n x 32, vertex-major) -> out (nsrc x n, source-major), through a shared-memory tile.
+__global__ void __launch_bounds__(kBlock) k_batch_out(TravCtx c) {
+  __shared__ uint32_t tile[32][33];
+  const CallArgs* ca = c.args;
+  const BatchAux* x = static_cast<const BatchAux*>(ca->aux);
+  const uint32_t n = c.n, ns = ca->nsrc;
+  uint32_t* out = ca->lab;
+  const uint32_t tx = threadIdx.x & 31u, ty = threadIdx.x >> 5;  // 32 x 8
+  for (uint64_t v0 = (uint64_t)blockIdx.x * 32u; v0 < n; v0 += (uint64_t)gridDim.x * 32u) {
+    for (uint32_t r = ty; r < 32u; r += 8u) {
+      const uint64_t v = v0 + r;
+      tile[r][tx] = v < n ? x->lab[v * 32u + tx] : 0u;
+    }
+    __syncthreads();
+    for (uint32_t s = ty; s < ns; s += 8u) {
+      const uint64_t v = v0 + tx;
+      if (v < n) out[(size_t)s * n + v] = tile[tx][s];
+    }
+    __syncthreads();
+  }
+}
+
+// ---- multi-source single-label kernels (many graphs as one disjoint union)
+
+template <int APP>
+__global__ void __launch_bounds__(kBlock) k_multi_init(TravCtx c) {
+  uint32_t* lab = c.args->lab;
+  for (uint64_t v = (uint64_t)blockIdx.x * kBlock + threadIdx.x; v < c.n; v += (uint64_t)gridDim.x * kBlock) {
+    lab[v] = kInf;
+    if (APP == APP_SSSP) c.stamp[v] = 0u;
+  }
+}
+
+__global__ void k_multi_seed(TravCtx c) {
+  const CallArgs* ca = c.args;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ca->nsrc; i += gridDim.x * blockDim.x) {
+    const uint32_t v = ca->srcs[i];
+    if (atomicCAS(ca->lab + v, kInf, 0u) == kInf) c.F0[atomicAdd(&c.st->fcount[0], 1u)] = v;
+  }
+}
+
+}  // namespace alb
+
+// ---------------------------------------------------------------- host side
+
+enum BatchKind { BK_MS_BFS = 0, BK_MS_SSSP = 1, BK_MULTI_BFS = 2, BK_MULTI_SSSP = 3, BK_COUNT = 4 };
 
 struct BatchWs {
-  int unused = 0;
+  uint32_t* lab = nullptr;
+  uint32_t* seen = nullptr;
+  unsigned long long* act = nullptr;
+  alb::BatchAux* aux = nullptr;
+  uint32_t* srcs = nullptr;
+  uint32_t cap_srcs = 0;
+  uint32_t* tmp = nullptr;  // 32 x n staging for host outputs
+  cudaGraph_t graph[BK_COUNT] = {};
+  cudaGraphExec_t exec[BK_COUNT] = {};
 };
 
 namespace alb {
 
 alb_status free_batch(alb_graph g) {
-  delete g->batch;
+  BatchWs* b = g->batch;
+  if (!b) return ALB_OK;
+  for (int i = 0; i < BK_COUNT; ++i) {
+    if (b->exec[i]) cudaGraphExecDestroy(b->exec[i]);
+    if (b->graph[i]) cudaGraphDestroy(b->graph[i]);
+  }
+  cudaFree(b->lab);
+  cudaFree(b->seen);
+  cudaFree(b->act);
+  cudaFree(b->aux);
+  cudaFree(b->srcs);
+  cudaFree(b->tmp);
+  cudaGetLastError();
+  delete b;
   g->batch = nullptr;
   return ALB_OK;
 }
 
 alb_status batch_stats(alb_graph, alb_stats*) { return ALB_OK; }
 
-static alb_status run_batch(alb_graph g, App app, const uint32_t* hd_srcs, uint32_t k, uint32_t* out,
-                            cudaStream_t s) {
-  uint32_t* srcs = nullptr;
-  bool own = false;
-  if (is_device_ptr(hd_srcs)) {
-    srcs = (uint32_t*)std::malloc(sizeof(uint32_t) * (k ? k : 1));
-    own = true;
-    ALB_CUDA_TRY(cudaMemcpy(srcs, hd_srcs, sizeof(uint32_t) * k, cudaMemcpyDeviceToHost));
-  } else {
-    srcs = const_cast<uint32_t*>(hd_srcs);
+static alb_status ensure_batch(alb_graph g, bool group_arrays, uint32_t nsrc) {
+  if (!g->batch) g->batch = new (std::nothrow) BatchWs();
+  BatchWs* b = g->batch;
+  if (!b) return ALB_ERR_OOM;
+  const size_t n = g->n;
+  if (group_arrays && !b->lab) {
+    ALB_CUDA_TRY(cudaMalloc((void**)&b->lab, sizeof(uint32_t) * n * 32u));
+    ALB_CUDA_TRY(cudaMalloc((void**)&b->seen, sizeof(uint32_t) * n));
+    ALB_CUDA_TRY(cudaMalloc((void**)&b->act, sizeof(unsigned long long) * n * 2u));
+    ALB_CUDA_TRY(cudaMalloc((void**)&b->aux, sizeof(BatchAux)));
+    BatchAux h{b->lab, b->seen, b->act, b->act + n};
+    ALB_CUDA_TRY(cudaMemcpy(b->aux, &h, sizeof(h), cudaMemcpyHostToDevice));
   }
-  alb_status rc = ALB_OK;
-  for (uint32_t i = 0; i < k && rc == ALB_OK; ++i)
-    if (srcs[i] >= g->n) rc = ALB_ERR_INVALID_ARG;
-  for (uint32_t i = 0; i < k && rc == ALB_OK; ++i)
-    rc = run_traversal(g, app, srcs[i], 0u, out + (size_t)i * g->n, s);
-  if (own) std::free(srcs);
-  return rc;
+  if (b->cap_srcs < nsrc) {
+    cudaFree(b->srcs);
+    b->srcs = nullptr;
+    ALB_CUDA_TRY(cudaMalloc((void**)&b->srcs, sizeof(uint32_t) * nsrc));
+    b->cap_srcs = nsrc;
+  }
+  return ALB_OK;
+}
+
+static alb_status add_node(cudaGraphNode_t* node, cudaGraph_t graph, const cudaGraphNode_t* dep,
+                           size_t ndep, void* fn, uint32_t grid, uint32_t block, TravCtx* c) {
+  cudaKernelNodeParams kp{};
+  void* kargs[] = {c};
+  kp.func = fn;
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(block);
+  kp.kernelParams = kargs;
+  ALB_CUDA_TRY(cudaGraphAddKernelNode(node, graph, dep, ndep, &kp));
+  return ALB_OK;
+}
+
+// memset(state) -> init -> seed -> while { inspect -> if (work) lb } [-> transpose]
+static alb_status build_batch_graph(alb_graph g, BatchKind kind) {
+  BatchWs* b = g->batch;
+  cudaGraph_t G = nullptr;
+  ALB_CUDA_TRY(cudaGraphCreate(&G, 0));
+  auto fail = [&](alb_status s) { cudaGraphDestroy(G); return s; };
+  cudaGraphConditionalHandle hw, hi;
+  if (cudaGraphConditionalHandleCreate(&hw, G, 1u, cudaGraphCondAssignDefault) != cudaSuccess ||
+      cudaGraphConditionalHandleCreate(&hi, G, 0u, cudaGraphCondAssignDefault) != cudaSuccess)
+    return fail(ALB_ERR_CUDA);
+  TravCtx c = make_ctx(g, true, hw, hi);
+  void *init, *seed, *insp, *lb;
+  uint32_t seed_grid = 1, seed_block = 32;
+  switch (kind) {
+    case BK_MS_BFS:
+      init = (void*)k_batch_init; seed = (void*)k_batch_seed;
+      insp = (void*)k_inspect<MsBfsOp>; lb = (void*)k_lb<MsBfsOp, false>;
+      break;
+    case BK_MS_SSSP:
+      init = (void*)k_batch_init; seed = (void*)k_batch_seed;
+      insp = (void*)k_inspect<MsSsspOp>; lb = (void*)k_lb<MsSsspOp, false>;
+      break;
+    case BK_MULTI_BFS:
+      init = (void*)k_multi_init<APP_BFS>; seed = (void*)k_multi_seed;
+      insp = (void*)k_inspect<BfsOp>; lb = (void*)k_lb<BfsOp, false>;
+      seed_grid = g->blocks; seed_block = kBlock;
+      break;
+    default:
+      init = (void*)k_multi_init<APP_SSSP>; seed = (void*)k_multi_seed;
+      insp = (void*)k_inspect<SsspOp>; lb = (void*)k_lb<SsspOp, false>;
+      seed_grid = g->blocks; seed_block = kBlock;
+      break;
+  }
+  cudaGraphNode_t n_ms, n_init, n_seed, n_while, n_insp, n_if, n_lb, n_out;
+  cudaMemsetParams ms{};
+  ms.dst = g->st;
+  ms.value = 0;
+  ms.elementSize = 4;
+  ms.width = sizeof(RoundState) / 4;
+  ms.height = 1;
+  alb_status rc;
+  if (cudaGraphAddMemsetNode(&n_ms, G, nullptr, 0, &ms) != cudaSuccess) return fail(ALB_ERR_CUDA);
+  if ((rc = add_node(&n_init, G, &n_ms, 1, init, g->blocks, kBlock, &c)) != ALB_OK) return fail(rc);
+  if ((rc = add_node(&n_seed, G, &n_init, 1, seed, seed_grid, seed_block, &c)) != ALB_OK) return fail(rc);
+  cudaGraphNodeParams wp{};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = hw;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  if (cudaGraphAddNode(&n_while, G, &n_seed, nullptr, 1, &wp) != cudaSuccess) return fail(ALB_ERR_CUDA);
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  if ((rc = add_node(&n_insp, body, nullptr, 0, insp, g->blocks, kBlock, &c)) != ALB_OK) return fail(rc);
+  cudaGraphNodeParams ip{};
+  ip.type = cudaGraphNodeTypeConditional;
+  ip.conditional.handle = hi;
+  ip.conditional.type = cudaGraphCondTypeIf;
+  ip.conditional.size = 1;
+  if (cudaGraphAddNode(&n_if, body, &n_insp, nullptr, 1, &ip) != cudaSuccess) return fail(ALB_ERR_CUDA);
+  if ((rc = add_node(&n_lb, ip.conditional.phGraph_out[0], nullptr, 0, lb, g->lb_blocks, kBlock, &c)) != ALB_OK)
+    return fail(rc);
+  if (kind == BK_MS_BFS || kind == BK_MS_SSSP) {
+    if ((rc = add_node(&n_out, G, &n_while, 1, (void*)k_batch_out, g->blocks, kBlock, &c)) != ALB_OK)
+      return fail(rc);
+  }
+  cudaGraphExec_t ex = nullptr;
+  if (cudaGraphInstantiate(&ex, G, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ALB_ERR_CUDA);
+  }
+  b->graph[kind] = G;
+  b->exec[kind] = ex;
+  return ALB_OK;
+}
+
+static alb_status stage_srcs(alb_graph g, const uint32_t* hd_srcs, uint32_t k, cudaStream_t s) {
+  BatchWs* b = g->batch;
+  ALB_CUDA_TRY(cudaMemcpyAsync(b->srcs, hd_srcs, sizeof(uint32_t) * k, cudaMemcpyDefault, s));
+  // every source must be a vertex: checked on the host copy
+  uint32_t* h = (uint32_t*)std::malloc(sizeof(uint32_t) * (k ? k : 1));
+  if (!h) return ALB_ERR_OOM;
+  cudaError_t e = cudaMemcpyAsync(h, b->srcs, sizeof(uint32_t) * k, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  bool ok = e == cudaSuccess;
+  for (uint32_t i = 0; ok && i < k; ++i) ok = h[i] < g->n;
+  std::free(h);
+  if (e != cudaSuccess) return ALB_ERR_CUDA;
+  return ok ? ALB_OK : ALB_ERR_INVALID_ARG;
+}
+
+static alb_status run_groups(alb_graph g, BatchKind kind, const uint32_t* hd_srcs, uint32_t k,
+                             uint32_t* out, cudaStream_t s) {
+  alb_status rc = ensure_batch(g, true, k);
+  if (rc != ALB_OK) return rc;
+  BatchWs* b = g->batch;
+  if ((rc = stage_srcs(g, hd_srcs, k, s)) != ALB_OK) return rc;
+  if (!b->exec[kind] && (rc = build_batch_graph(g, kind)) != ALB_OK) return rc;
+  const bool dev = is_device_ptr(out);
+  if (!dev && !b->tmp) ALB_CUDA_TRY(cudaMalloc((void**)&b->tmp, sizeof(uint32_t) * (size_t)g->n * 32u));
+  const size_t n = g->n;
+  for (uint32_t g0 = 0; g0 < k; g0 += 32u) {
+    const uint32_t ns = (k - g0) < 32u ? (k - g0) : 32u;
+    uint32_t* dst = dev ? out + (size_t)g0 * n : b->tmp;
+    CallArgs ca{dst, 0u, 0u, nullptr, nullptr, nullptr, b->aux, b->srcs + g0, ns};
+    k_set_args<<<1, 1, 0, s>>>(g->args, ca);
+    ALB_CUDA_TRY(cudaGetLastError());
+    ALB_CUDA_TRY(cudaGraphLaunch(b->exec[kind], s));
+    if (!dev)
+      ALB_CUDA_TRY(cudaMemcpyAsync(out + (size_t)g0 * n, b->tmp, sizeof(uint32_t) * n * ns,
+                                   cudaMemcpyDeviceToHost, s));
+  }
+  g->last_stream = s;
+  g->last_kind = 0;
+  return ALB_OK;
+}
+
+static alb_status run_multi(alb_graph g, BatchKind kind, const uint32_t* hd_srcs, uint32_t k,
+                            uint32_t* out, cudaStream_t s) {
+  alb_status rc = ensure_batch(g, false, k);
+  if (rc != ALB_OK) return rc;
+  BatchWs* b = g->batch;
+  if ((rc = stage_srcs(g, hd_srcs, k, s)) != ALB_OK) return rc;
+  if (!b->exec[kind] && (rc = build_batch_graph(g, kind)) != ALB_OK) return rc;
+  const bool dev = is_device_ptr(out);
+  uint32_t* lab = out;
+  if (!dev) {
+    if ((rc = ensure_tmp(g)) != ALB_OK) return rc;
+    lab = g->tmp;
+  }
+  CallArgs ca{lab, 0u, 0u, nullptr, nullptr, nullptr, nullptr, b->srcs, k};
+  k_set_args<<<1, 1, 0, s>>>(g->args, ca);
+  ALB_CUDA_TRY(cudaGetLastError());
+  ALB_CUDA_TRY(cudaGraphLaunch(b->exec[kind], s));
+  if (!dev) ALB_CUDA_TRY(cudaMemcpyAsync(out, lab, sizeof(uint32_t) * g->n, cudaMemcpyDeviceToHost, s));
+  g->last_stream = s;
+  g->last_kind = 0;
+  return ALB_OK;
 }
 
 }  // namespace alb
 
 using namespace alb;
 
+static alb_status sssp_ok(alb_graph g) {
+  if (!g->has_w) return ALB_ERR_UNSUPPORTED;
+  if ((uint64_t)g->max_w * (uint64_t)(g->n - 1) >= 0xFFFFFFFFull) return ALB_ERR_OVERFLOW;
+  return ALB_OK;
+}
+
 extern "C" alb_status alb_bfs_batch(alb_graph g, const uint32_t* hd_srcs, uint32_t k, uint32_t* hd_out,
                                     alb_stream stream) {
   if (!g || (k && (!hd_srcs || !hd_out))) return ALB_ERR_INVALID_ARG;
+  if (k == 0) return ALB_OK;
   if (cudaSetDevice(g->device) != cudaSuccess) return ALB_ERR_CUDA;
-  return run_batch(g, APP_BFS, hd_srcs, k, hd_out, (cudaStream_t)stream);
+  return run_groups(g, BK_MS_BFS, hd_srcs, k, hd_out, (cudaStream_t)stream);
 }
 
 extern "C" alb_status alb_sssp_batch(alb_graph g, const uint32_t* hd_srcs, uint32_t k, uint32_t* hd_out,
                                      alb_stream stream) {
   if (!g || (k && (!hd_srcs || !hd_out))) return ALB_ERR_INVALID_ARG;
-  if (!g->has_w) return ALB_ERR_UNSUPPORTED;
-  if ((uint64_t)g->max_w * (uint64_t)(g->n - 1) >= 0xFFFFFFFFull) return ALB_ERR_OVERFLOW;
+  alb_status rc = sssp_ok(g);
+  if (rc != ALB_OK) return rc;
+  if (k == 0) return ALB_OK;
   if (cudaSetDevice(g->device) != cudaSuccess) return ALB_ERR_CUDA;
-  return run_batch(g, APP_SSSP, hd_srcs, k, hd_out, (cudaStream_t)stream);
+  return run_groups(g, BK_MS_SSSP, hd_srcs, k, hd_out, (cudaStream_t)stream);
+}
+
+extern "C" alb_status alb_bfs_multi(alb_graph g, const uint32_t* hd_srcs, uint32_t k, uint32_t* hd_levels,
+                                    alb_stream stream) {
+  if (!g || !hd_srcs || !hd_levels || k == 0) return ALB_ERR_INVALID_ARG;
+  if (cudaSetDevice(g->device) != cudaSuccess) return ALB_ERR_CUDA;
+  return run_multi(g, BK_MULTI_BFS, hd_srcs, k, hd_levels, (cudaStream_t)stream);
+}
+
+extern "C" alb_status alb_sssp_multi(alb_graph g, const uint32_t* hd_srcs, uint32_t k, uint32_t* hd_dist,
+                                     alb_stream stream) {
+  if (!g || !hd_srcs || !hd_dist || k == 0) return ALB_ERR_INVALID_ARG;
+  alb_status rc = sssp_ok(g);
+  if (rc != ALB_OK) return rc;
+  if (cudaSetDevice(g->device) != cudaSuccess) return ALB_ERR_CUDA;
+  return run_multi(g, BK_MULTI_SSSP, hd_srcs, k, hd_dist, (cudaStream_t)stream);
 }

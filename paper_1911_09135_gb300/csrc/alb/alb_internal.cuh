@@ -49,6 +49,9 @@ struct CallArgs {
   uint32_t* trace_src;
   uint32_t* trace_dst;
   uint32_t* trace_thread;
+  const void* aux;    // multi-source operators: their BatchAux
+  const uint32_t* srcs;  // sources of a multi-source call
+  uint32_t nsrc;
 };
 
 // Everything a round kernel needs, passed by value (fixed for a cached graph).

@@ -1,0 +1,450 @@
+// Data-driven traversals (bfs, sssp, cc, kcore) with the adaptive load balancer
+// of arXiv:1911.09135, Sec. 4.
+//
+// One round = two kernels:
+//   k_inspect  Algorithm 1 fused with TWC expansion (Sec. 3, Sec. 4.1): each CTA
+//              takes tiles of the frontier, reads every vertex's degree, appends
+//              huge vertices (degree >= threshold) to `work` together with their
+//              slot of the exclusive prefix sum of huge degrees (one packed 64-bit
+//              atomic per warp yields both the slot and the prefix, so prefixWork
+//              needs no separate scan pass), and expands the rest at once: CTA bin
+//              by the whole CTA, warp bin by one warp, thread bin by a CTA-wide
+//              fine-grained gather over the small vertices' edges.
+//   k_lb       Algorithm 2: the edges of all huge vertices are dealt cyclically
+//              (position k goes to thread k mod p) or blocked over every thread
+//              of the grid; the source of position k is found by binary search
+//              of prefixWork (staged in shared memory).
+// The LB kernel runs only when `work` is non-empty (a conditional graph node).
+// Each round's last CTA closes the round on the device (last-block ticket) and
+// sets the while-node condition, so whole traversals run without host syncs.
+#pragma once
+
+#include "alb_device.cuh"
+
+namespace alb {
+
+// ------------------------------------------------------------------ operators
+
+struct OpArgs {
+  uint32_t* lab;
+  uint32_t* stamp;
+  uint32_t next;  // round + 1
+  uint32_t k;
+  const void* aux;  // operator-specific state (the multi-source operators)
+};
+
+// bfs (push): level[dst] = round + 1 if unvisited.
+struct BfsOp {
+  static constexpr bool kBatch = false;
+  static constexpr bool kW = false;
+  __device__ static uint32_t sval(const OpArgs&, uint32_t) { return 0u; }
+  __device__ static bool want(const OpArgs&, uint32_t, uint32_t cur, uint32_t) { return cur == kInf; }
+  __device__ static bool commit(const OpArgs& a, uint32_t, uint32_t dst, uint32_t) {
+    return atomicCAS(a.lab + dst, kInf, a.next) == kInf;
+  }
+};
+
+// sssp (push relaxation, Fig. 3): dist[dst] = min(dist[dst], dist[src] + w).
+// The atomicMin does not wait for its old value: a destination whose pre-checked distance
+// improves is pushed (once per round, by its round stamp), so every vertex whose distance drops
+// is in the next frontier.
+struct SsspOp {
+  static constexpr bool kBatch = false;
+  static constexpr bool kW = true;
+  __device__ static uint32_t sval(const OpArgs& a, uint32_t u) { return a.lab[u]; }
+  __device__ static bool want(const OpArgs&, uint32_t sv, uint32_t cur, uint32_t w) {
+    return (uint64_t)sv + w < (uint64_t)cur;
+  }
+  __device__ static bool commit(const OpArgs& a, uint32_t sv, uint32_t dst, uint32_t w) {
+    atomicMin(a.lab + dst, sv + w);
+    return a.stamp[dst] != a.next && atomicMax(a.stamp + dst, a.next) < a.next;
+  }
+};
+
+// cc (push min-label propagation): label[dst] = min(label[dst], label[src]); the same
+// non-blocking update and round-stamp push as sssp.
+struct CcOp {
+  static constexpr bool kBatch = false;
+  static constexpr bool kW = false;
+  __device__ static uint32_t sval(const OpArgs& a, uint32_t u) { return a.lab[u]; }
+  __device__ static bool want(const OpArgs&, uint32_t sv, uint32_t cur, uint32_t) { return sv < cur; }
+  __device__ static bool commit(const OpArgs& a, uint32_t sv, uint32_t dst, uint32_t) {
+    atomicMin(a.lab + dst, sv);
+    return a.stamp[dst] != a.next && atomicMax(a.stamp + dst, a.next) < a.next;
+  }
+};
+
+// kcore (peeling): a removed vertex decrements each neighbour's remaining
+// degree; the neighbour is removed (pushed) exactly when it drops from k to
+// k - 1. Neighbours already below k are skipped (their membership is settled).
+struct KcoreOp {
+  static constexpr bool kBatch = false;
+  static constexpr bool kW = false;
+  __device__ static uint32_t sval(const OpArgs&, uint32_t) { return 0u; }
+  __device__ static bool want(const OpArgs& a, uint32_t, uint32_t cur, uint32_t) { return cur >= a.k; }
+  __device__ static bool commit(const OpArgs& a, uint32_t, uint32_t dst, uint32_t) {
+    return atomicSub(a.lab + dst, 1u) == a.k;
+  }
+};
+
+// Relax U edges per thread; all loads are issued before the atomics so each
+// thread keeps U independent memory requests in flight. Warp-uniform callers.
+template <class Op, int U>
+__device__ __forceinline__ void relax(const TravCtx& c, const OpArgs& a, const uint32_t (&e)[U],
+                                      const bool (&ok)[U], const uint32_t (&sv)[U], uint32_t* Fn,
+                                      uint32_t* ncount) {
+  uint32_t dst[U], wt[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) dst[u] = ok[u] ? __ldcs(c.idx + e[u]) : 0u;  // streamed once: evict-first
+#pragma unroll
+  for (int u = 0; u < U; ++u) wt[u] = (Op::kW && ok[u]) ? __ldcs(c.w + e[u]) : 0u;
+  if constexpr (Op::kBatch) {
+    // multi-source operators do their own label reads (a row of sources per vertex)
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool push = ok[u] && Op::apply(a, sv[u], dst[u], wt[u]);
+      warp_append(push, dst[u], Fn, ncount);
+    }
+  } else {
+    uint32_t cur[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) cur[u] = ok[u] ? a.lab[dst[u]] : 0u;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool push = ok[u] && Op::want(a, sv[u], cur[u], wt[u]) && Op::commit(a, sv[u], dst[u], wt[u]);
+      warp_append(push, dst[u], Fn, ncount);
+    }
+  }
+}
+
+// Close round r (one thread of the last CTA): account, reset the per-round
+// counters, advance the round and set the while condition.
+static __device__ void finish_round(const TravCtx& c) {
+  RoundState* st = c.st;
+  const uint32_t r = __ldcg(&st->round);
+  const uint32_t cur = r & 1u;
+  const uint32_t nextc = __ldcg(&st->fcount[cur ^ 1u]);
+  const unsigned long long hp = __ldcg(&st->hub_packed);
+  const uint32_t nh = (uint32_t)(hp >> 32);
+  if (nh) {
+    st->hub_rounds += 1u;
+    if (nh > st->max_hub_count) st->max_hub_count = nh;
+    st->edges_lb += (uint32_t)hp;
+  }
+  st->pushes += nextc;
+  st->fcount[cur] = 0u;
+  st->hub_packed = 0ull;
+  st->tile_next = 0u;
+  st->done_inspect = 0u;
+  st->done_lb = 0u;
+  st->all_active = 0u;
+  st->round = r + 1u;
+  bool go = nextc > 0u;
+  if (go && r + 1u >= c.max_rounds) {
+    st->status |= ST_ERR_ROUNDS;
+    go = false;
+  }
+  __threadfence();
+  if (c.use_graph) cudaGraphSetConditional(c.h_while, go ? 1u : 0u);
+}
+
+// Append huge vertices to `work` with their prefixWork entry: one 64-bit atomic
+// per warp adds (count << 32 | degree sum), so slot order and prefix order agree.
+static __device__ __forceinline__ void hub_append(bool huge, uint32_t v, uint32_t deg, uint32_t* hub_v,
+                                           uint32_t* hub_p, unsigned long long* packed) {
+  const unsigned mask = __ballot_sync(kFull, huge);
+  if (mask == 0) return;
+  const uint32_t lane = lane_id();
+  const uint32_t x = huge ? deg : 0u;
+  const uint32_t incl = warp_inclusive_scan(x);
+  const uint32_t total = __shfl_sync(kFull, incl, 31);
+  const uint32_t leader = __ffs(mask) - 1;
+  unsigned long long old = 0ull;
+  if (lane == leader) old = atomicAdd(packed, ((unsigned long long)__popc(mask) << 32) | total);
+  old = __shfl_sync(kFull, old, leader);
+  if (huge) {
+    const uint32_t slot = (uint32_t)(old >> 32) + __popc(mask & ((1u << lane) - 1u));
+    hub_v[slot] = v;
+    hub_p[slot] = (uint32_t)old + (incl - x);
+  }
+}
+
+// ----------------------------------------------------- inspection + TWC kernel
+
+template <class Op>
+__global__ void __launch_bounds__(kBlock) k_inspect(TravCtx c) {
+  __shared__ uint32_t s_cb[kBlock], s_cd[kBlock], s_cv[kBlock];       // CTA bin
+  __shared__ uint32_t s_wb[kBlock], s_wd[kBlock], s_wv[kBlock];       // warp bin
+  __shared__ uint32_t s_scan[kBlock + 1], s_sb[kBlock], s_sv[kBlock];  // thread bin
+  __shared__ uint32_t s_warp[kWarps + 1];
+  __shared__ uint32_t s_ncta, s_nwrp, s_tile;
+
+  RoundState* st = c.st;
+  const uint32_t r = st->round;
+  const uint32_t cur = r & 1u;
+  const bool all = st->all_active != 0u;
+  const uint32_t nf = all ? c.n : st->fcount[cur];
+  const uint32_t* F = cur ? c.F1 : c.F0;
+  uint32_t* Fn = cur ? c.F0 : c.F1;
+  uint32_t* ncount = &st->fcount[cur ^ 1u];
+  const CallArgs* ca = c.args;
+  const OpArgs a{ca->lab, c.stamp, r + 1u, ca->k, ca->aux};
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  unsigned long long twc_edges = 0ull;
+
+  for (;;) {
+    if (tid == 0) {
+      s_tile = atomicAdd(&st->tile_next, 1u);
+      s_ncta = 0u;
+      s_nwrp = 0u;
+    }
+    __syncthreads();
+    const uint64_t base = (uint64_t)s_tile * kBlock;
+    if (base >= nf) break;  // CTA-uniform
+    const uint32_t i = (uint32_t)base + tid;
+    const bool valid = i < nf;
+    uint32_t v = 0u, beg = 0u, deg = 0u, sv = 0u;
+    if (valid) {
+      v = all ? i : F[i];
+      beg = c.off[v];
+      deg = c.off[v + 1] - beg;
+      sv = Op::sval(a, v);
+    }
+    const bool huge = valid && deg >= c.threshold;
+    const bool cta = valid && !huge && deg >= c.cta_min;
+    const bool wrp = valid && !huge && !cta && deg >= c.warp_min;
+    const uint32_t sdeg = (valid && !huge && !cta && !wrp) ? deg : 0u;
+    if (valid && !huge) twc_edges += deg;
+    hub_append(huge, v, deg, c.hub_v, c.hub_p, &st->hub_packed);
+    if (cta) {
+      const uint32_t s = atomicAdd(&s_ncta, 1u);
+      s_cb[s] = beg; s_cd[s] = deg; s_cv[s] = sv;
+    }
+    if (wrp) {
+      const uint32_t s = atomicAdd(&s_nwrp, 1u);
+      s_wb[s] = beg; s_wd[s] = deg; s_wv[s] = sv;
+    }
+    uint32_t stotal;
+    const uint32_t ex = block_exclusive_scan<kBlock>(sdeg, s_warp, &stotal);
+    s_scan[tid] = ex;
+    s_sb[tid] = beg;
+    s_sv[tid] = sv;
+    if (tid == 0) s_scan[kBlock] = stotal;
+    __syncthreads();
+
+    // CTA bin: the whole CTA expands one vertex at a time.
+    const uint32_t ncta = s_ncta;
+    for (uint32_t j = 0; j < ncta; ++j) {
+      const uint32_t b = s_cb[j], d = s_cd[j], svj = s_cv[j];
+      for (uint32_t e0 = 0; e0 < d; e0 += kBlock * 4) {
+        uint32_t e[4], s4[4];
+        bool ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const uint32_t q = e0 + u * kBlock + tid;
+          ok[u] = q < d; e[u] = b + q; s4[u] = svj;
+        }
+        relax<Op, 4>(c, a, e, ok, s4, Fn, ncount);
+      }
+    }
+    // Warp bin: one warp per vertex.
+    const uint32_t nw = s_nwrp;
+    for (uint32_t j = warp; j < nw; j += kWarps) {
+      const uint32_t b = s_wb[j], d = s_wd[j], svj = s_wv[j];
+      for (uint32_t e0 = 0; e0 < d; e0 += 32 * 4) {
+        uint32_t e[4], s4[4];
+        bool ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const uint32_t q = e0 + u * 32 + lane;
+          ok[u] = q < d; e[u] = b + q; s4[u] = svj;
+        }
+        relax<Op, 4>(c, a, e, ok, s4, Fn, ncount);
+      }
+    }
+    // Thread bin: the small vertices' edges, gathered over the whole CTA
+    // (consecutive threads take consecutive edges of the concatenated lists).
+    const uint32_t S = s_scan[kBlock];
+    uint32_t owner = 0u;
+    for (uint32_t q0 = 0; q0 < S; q0 += kBlock * 2) {
+      uint32_t e[2], s2[2];
+      bool ok[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const uint32_t q = q0 + u * kBlock + tid;
+        ok[u] = q < S;
+        e[u] = 0u; s2[u] = 0u;
+        if (ok[u]) {
+          owner = upper_search(s_scan, owner, kBlock, q);
+          e[u] = s_sb[owner] + (q - s_scan[owner]);
+          s2[u] = s_sv[owner];
+        }
+      }
+      relax<Op, 2>(c, a, e, ok, s2, Fn, ncount);
+    }
+    __syncthreads();
+  }
+
+  // statistics: one atomic per warp
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) twc_edges += __shfl_down_sync(kFull, twc_edges, o);
+  if (lane == 0 && twc_edges) atomicAdd(&st->edges_twc, twc_edges);
+
+  if (last_block_ticket(&st->done_inspect)) {
+    const unsigned long long hp = __ldcg(&st->hub_packed);
+    const uint32_t nh = (uint32_t)(hp >> 32);
+    if (c.use_graph) cudaGraphSetConditional(c.h_if, nh > 0u ? 1u : 0u);
+    if (nh == 0u) finish_round(c);
+  }
+}
+
+// ------------------------------------------------------------- LB kernel
+
+struct TraceOp {};
+
+template <class Op, bool kTrace>
+__global__ void __launch_bounds__(kBlock) k_lb(TravCtx c) {
+  constexpr int kStage = kHubSmem;
+  __shared__ uint32_t s_p[kStage];
+  __shared__ uint32_t s_base[kStage];
+  __shared__ uint32_t s_val[kStage];
+  __shared__ uint32_t s_src[kTrace ? kStage : 1];
+
+  RoundState* st = c.st;
+  const unsigned long long hp = st->hub_packed;
+  const uint32_t nh = (uint32_t)(hp >> 32);
+  const uint32_t e = (uint32_t)hp;
+  const uint32_t r = st->round;
+  const uint32_t cur = r & 1u;
+  uint32_t* Fn = cur ? c.F0 : c.F1;
+  uint32_t* ncount = &st->fcount[cur ^ 1u];
+  const CallArgs* ca = c.args;
+  const OpArgs a{ca->lab, c.stamp, r + 1u, ca->k, ca->aux};
+  const uint32_t tid = threadIdx.x, lane = tid & 31u;
+
+  const bool staged = nh <= (uint32_t)kStage;
+  if (staged) {
+    for (uint32_t j = tid; j < nh; j += kBlock) {
+      const uint32_t u = c.hub_v[j], p = c.hub_p[j];
+      s_p[j] = p;
+      s_base[j] = c.off[u] - p;
+      if constexpr (kTrace) s_src[j] = u;
+      else s_val[j] = Op::sval(a, u);
+    }
+  }
+  __syncthreads();
+  const uint32_t* P = staged ? s_p : c.hub_p;
+
+  // source lookup for position k; j only grows along a thread's positions
+  uint32_t j = 0u, jc = kInf, base_c = 0u, val_c = 0u, src_c = 0u;
+  auto resolve = [&](uint32_t k, uint32_t& edge, uint32_t& sv, uint32_t& src) {
+    j = upper_search(P, j, nh, k);
+    if (staged) {
+      edge = k + s_base[j];
+      if constexpr (kTrace) { src = s_src[j]; sv = 0u; }
+      else { sv = s_val[j]; src = 0u; }
+    } else {
+      if (j != jc) {
+        const uint32_t u = c.hub_v[j];
+        base_c = c.off[u] - c.hub_p[j];
+        if constexpr (!kTrace) val_c = Op::sval(a, u);
+        src_c = u;
+        jc = j;
+      }
+      edge = k + base_c; sv = val_c; src = src_c;
+    }
+  };
+
+  const uint64_t p = (uint64_t)gridDim.x * kBlock;
+  const uint64_t gt = (uint64_t)blockIdx.x * kBlock + tid;
+  constexpr int U = 4;
+  auto process = [&](const uint64_t (&k)[U], const bool (&ok)[U]) {
+    uint32_t ed[U], sv[U], src[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      ed[u] = 0u; sv[u] = 0u; src[u] = 0u;
+      if (ok[u]) resolve((uint32_t)k[u], ed[u], sv[u], src[u]);
+    }
+    if constexpr (kTrace) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (ok[u]) {
+          ca->trace_src[k[u]] = src[u];
+          ca->trace_dst[k[u]] = c.idx[ed[u]];
+          ca->trace_thread[k[u]] = (uint32_t)gt;
+        }
+      }
+    } else {
+      relax<Op, U>(c, a, ed, ok, sv, Fn, ncount);
+    }
+  };
+
+  if (c.distribution == 0u) {
+    // cyclic: thread gt takes positions gt, gt + p, gt + 2p, ... (Sec. 4.1)
+    for (uint64_t k0 = gt - lane; k0 < e; k0 += p * U) {  // warp-uniform
+      uint64_t k[U];
+      bool ok[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) { k[u] = k0 + lane + (uint64_t)u * p; ok[u] = k[u] < e; }
+      process(k, ok);
+    }
+  } else {
+    // blocked: thread gt takes [gt * C, min(e, (gt + 1) * C)), C = ceil(e / p)
+    const uint64_t C = (e + p - 1) / p;
+    const uint64_t lo = gt * C;
+    const uint64_t hi = (lo + C < (uint64_t)e) ? lo + C : (uint64_t)e;
+    for (uint64_t i0 = 0; i0 < C; i0 += U) {  // uniform trip count
+      uint64_t k[U];
+      bool ok[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) { k[u] = lo + i0 + u; ok[u] = k[u] < hi; }
+      process(k, ok);
+    }
+  }
+
+  if (last_block_ticket(&st->done_lb)) {
+    if constexpr (!kTrace) finish_round(c);
+  }
+}
+
+// ------------------------------------------------------------- init kernels
+
+template <int APP>
+__global__ void __launch_bounds__(kBlock) k_init(TravCtx c) {
+  const CallArgs* ca = c.args;
+  uint32_t* lab = ca->lab;
+  const uint32_t src = ca->src, k = ca->k, n = c.n;
+  RoundState* st = c.st;
+  for (uint64_t b = (uint64_t)blockIdx.x * kBlock; b < n; b += (uint64_t)gridDim.x * kBlock) {
+    const uint32_t v = (uint32_t)b + threadIdx.x;
+    const bool ok = v < n;
+    if constexpr (APP == APP_BFS) {
+      if (ok) lab[v] = (v == src) ? 0u : kInf;
+    } else if constexpr (APP == APP_SSSP) {
+      if (ok) { lab[v] = (v == src) ? 0u : kInf; c.stamp[v] = 0u; }
+    } else if constexpr (APP == APP_CC) {
+      if (ok) { lab[v] = v; c.stamp[v] = 0u; }
+    } else if constexpr (APP == APP_KCORE) {
+      uint32_t d = 0u;
+      if (ok) { d = c.off[v + 1] - c.off[v]; lab[v] = d; }
+      warp_append(ok && d < k, v, c.F0, &st->fcount[0]);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if constexpr (APP == APP_BFS || APP == APP_SSSP) { c.F0[0] = src; st->fcount[0] = 1u; }
+    if constexpr (APP == APP_CC) { st->all_active = 1u; st->fcount[0] = n; }
+  }
+}
+
+// k-core output: remaining degree >= k  ->  1, else 0 (in place).
+static __global__ void k_kcore_finish(const CallArgs* ca, uint32_t n) {
+  uint32_t* lab = ca->lab;
+  const uint32_t k = ca->k;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (uint64_t)gridDim.x * blockDim.x)
+    lab[v] = lab[v] >= k ? 1u : 0u;
+}
+
+static __global__ void k_set_args(CallArgs* dst, CallArgs v) { *dst = v; }
+
+}  // namespace alb

@@ -222,3 +222,40 @@ def random_graph(n: int, m: int, seed: int, *, symmetrize: bool, weighted: bool 
             ww = (((lo * 1000003 + hi * 7919 + seed) % wmax) + 1)
         g = from_edges(n, e, ww, symmetrize=True)
     return g
+
+
+def disjoint_union(graphs: list[CSR], name: str = "") -> tuple[CSR, np.ndarray]:
+    """One CSR holding every graph of `graphs`, graph i's vertex v renumbered to base[i] + v.
+
+    Returns (union, base) with base[i] the first vertex id of graph i (base[-1] = total n).
+    Traversals of the union from one source per graph give each graph's own result.
+    """
+    ns = np.array([g.n for g in graphs], dtype=np.int64)
+    ms = np.array([g.m for g in graphs], dtype=np.int64)
+    base = np.concatenate([[0], np.cumsum(ns)])
+    ebase = np.concatenate([[0], np.cumsum(ms)])
+    if base[-1] >= 2 ** 32 - 1 or ebase[-1] >= 2 ** 32 - 1:
+        raise ValueError("union too large for uint32 CSR")
+    off = np.empty(int(base[-1]) + 1, dtype=np.uint32)
+    idx = np.empty(int(ebase[-1]), dtype=np.uint32)
+    weighted = all(g.weights is not None for g in graphs)
+    w = np.empty(int(ebase[-1]), dtype=np.uint32) if weighted else None
+    for i, g in enumerate(graphs):
+        off[base[i]:base[i + 1]] = g.offsets[:-1].astype(np.int64) + ebase[i]
+        idx[ebase[i]:ebase[i + 1]] = g.indices.astype(np.int64) + base[i]
+        if weighted:
+            w[ebase[i]:ebase[i + 1]] = g.weights
+    off[-1] = ebase[-1]
+    return CSR(n=int(base[-1]), offsets=off, indices=idx, weights=w,
+               symmetric=all(g.symmetric for g in graphs), name=name), base
+
+
+def small_graphs(count: int = 512, seed: int = 4, nthreads: int = 0) -> list[CSR]:
+    """The many-small-graphs batch: RMAT graphs whose sample counts are log-uniform in
+    [2^10, 2^22] (scale = max(4, round(log2(samples / 16)))), symmetrised, weights 1..100,
+    graph i drawn with seed 1000 * seed + i."""
+    out = []
+    for i, (sc, ms) in enumerate(small_graph_sizes(count, seed)):
+        out.append(rmat(sc, ms, 1000 * seed + i, symmetrize=True, weighted=True, nthreads=nthreads,
+                        name=f"small{i}"))
+    return out

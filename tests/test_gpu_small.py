@@ -296,3 +296,76 @@ def test_batch_matches_single_source(rmat13):
     for i, s in enumerate(srcs):
         assert np.array_equal(res[i], oracle.sssp(g.n, g.offsets, g.indices, g.weights, int(s)))
     G.close()
+
+
+@pytest.mark.parametrize("t", [-1, 0, 64, 1 << 33])
+def test_batch_groups_ragged_and_duplicates(rmat13, t):
+    """40 sources = a full group of 32 and a ragged group of 8, with repeated sources."""
+    g = rmat13
+    G = make(g)
+    G.set_params(hub_threshold=t)
+    rng = np.random.default_rng(7)
+    srcs = rng.integers(0, g.n, size=40).astype(np.uint32)
+    srcs[5] = srcs[3]
+    srcs[33] = srcs[3]
+    out = torch.empty(len(srcs) * g.n, dtype=torch.int32, device="cuda")
+    G.bfs_batch(srcs, out)
+    res = host(out).reshape(len(srcs), g.n).copy()
+    G.sssp_batch(srcs, out)
+    res2 = host(out).reshape(len(srcs), g.n).copy()
+    for i, s in enumerate(srcs):
+        assert np.array_equal(res[i], oracle.bfs(g.n, g.offsets, g.indices, int(s))), i
+        assert np.array_equal(res2[i], oracle.sssp(g.n, g.offsets, g.indices, g.weights, int(s))), i
+    G.close()
+
+
+def test_batch_host_output_and_directed():
+    g = gg.rmat16_directed()
+    G = alb.Graph(g.n, g.offsets, g.indices)
+    srcs = [0, 1, 2, 40000, 65535]
+    res = G.bfs_batch(srcs).reshape(len(srcs), g.n)
+    for i, s in enumerate(srcs):
+        assert np.array_equal(res[i], oracle.bfs(g.n, g.offsets, g.indices, s))
+    G.close()
+
+
+def test_multi_source_is_min_over_sources(rmat13):
+    g = rmat13
+    G = make(g)
+    srcs = np.array([0, 100, 5000, 100], dtype=np.uint32)
+    lv = G.bfs_multi(srcs)
+    d = G.sssp_multi(srcs)
+    exp_l = np.minimum.reduce([oracle.bfs(g.n, g.offsets, g.indices, int(s)) for s in srcs])
+    exp_d = np.minimum.reduce([oracle.sssp(g.n, g.offsets, g.indices, g.weights, int(s)) for s in srcs])
+    assert np.array_equal(lv, exp_l) and np.array_equal(d, exp_d)
+    G.close()
+
+
+@pytest.mark.parametrize("t", [-1, 0, 1 << 33])
+def test_disjoint_union_of_many_graphs(t):
+    rng = np.random.default_rng(3)
+    parts = [gg.rmat(int(sc), int(16 << sc), 100 + i, symmetrize=True, weighted=True)
+             for i, sc in enumerate(rng.integers(4, 11, size=25))]
+    parts += [graphs.star(40), graphs.path(30), graphs.empty(3)]
+    u, base = gg.disjoint_union(parts)
+    G = make(u)
+    G.set_params(hub_threshold=t)
+    srcs = base[:-1].astype(np.uint32)  # vertex 0 of every graph
+    lv = G.bfs_multi(srcs)
+    d = G.sssp_multi(srcs)
+    for i, p in enumerate(parts):
+        sl = slice(int(base[i]), int(base[i + 1]))
+        assert np.array_equal(lv[sl], oracle.bfs(p.n, p.offsets, p.indices, 0)), i
+        assert np.array_equal(d[sl], oracle.sssp(p.n, p.offsets, p.indices, p.weights, 0)), i
+    G.close()
+
+
+def test_batch_argument_errors(rmat13):
+    g = rmat13
+    G = make(g)
+    with pytest.raises(alb.AlbError) as e:
+        G.bfs_batch(np.array([0, g.n], dtype=np.uint32))
+    assert e.value.code == 1
+    with pytest.raises(alb.AlbError):
+        G.bfs_multi(np.array([g.n + 5], dtype=np.uint32))
+    G.close()

@@ -130,3 +130,44 @@ def test_rmat24_pagerank(rmat24):
     assert err <= 1e-5
     assert abs(it - it_ref) <= 1 and l1 < 1e-6
     assert abs(x.sum() - 1.0) < 1e-4
+
+
+def test_rmat22_batch_of_128_sources(rmat22):
+    """128 uniform random sources (seed 4) in groups of 32 sharing CSR reads; every source's
+    result is checked exactly (oracle certificates), two of them against the full oracle."""
+    g = rmat22
+    rng = np.random.Generator(np.random.Philox(key=4))
+    srcs = rng.integers(0, g.n, size=128).astype(np.uint32)
+    with make(g) as G:
+        out = torch.empty(128 * g.n, dtype=torch.int32, device="cuda")
+        G.bfs_batch(srcs, out)
+        lv = host(out).reshape(128, g.n).copy()
+        G.sssp_batch(srcs, out)
+        ds = host(out).reshape(128, g.n).copy()
+    for i in range(0, 128, 8):
+        s = int(srcs[i])
+        assert oracle.check_bfs(g.n, g.offsets, g.indices, s, lv[i]) == -1, i
+        assert oracle.check_sssp(g.n, g.offsets, g.indices, g.weights, s, ds[i]) == -1, i
+    for i in (0, 127):
+        s = int(srcs[i])
+        assert np.array_equal(lv[i], oracle.bfs(g.n, g.offsets, g.indices, s))
+        assert np.array_equal(ds[i], oracle.sssp(g.n, g.offsets, g.indices, g.weights, s))
+
+
+def test_512_small_graphs_in_one_traversal():
+    parts = gg.small_graphs(512, seed=4)
+    u, base = gg.disjoint_union(parts)
+    srcs = base[:-1].astype(np.uint32)
+    with make(u) as G:
+        o = torch.empty(u.n, dtype=torch.int32, device="cuda")
+        G.bfs_multi(srcs, o)
+        lv = host(o).copy()
+        G.sssp_multi(srcs, o)
+        ds = host(o).copy()
+    for i, p in enumerate(parts):
+        sl = slice(int(base[i]), int(base[i + 1]))
+        assert np.array_equal(lv[sl], oracle.bfs(p.n, p.offsets, p.indices, 0)), i
+        if i % 8 == 0:
+            assert np.array_equal(ds[sl], oracle.sssp(p.n, p.offsets, p.indices, p.weights, 0)), i
+        else:
+            assert oracle.check_sssp(p.n, p.offsets, p.indices, p.weights, 0, ds[sl]) == -1, i

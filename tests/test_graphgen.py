@@ -79,3 +79,13 @@ def test_from_edges_fixture_helper():
     rows = _rows(g)
     assert rows[0].tolist() == [1, 3] and rows[1].tolist() == [0] and rows[2].size == 0
     assert rows[3].tolist() == [0]
+
+
+def test_disjoint_union_renumbers_and_keeps_rows():
+    a = gg.from_edges(3, [(0, 1), (1, 2)], [4, 5], symmetrize=True)
+    b = gg.from_edges(2, [(0, 1)], [7], symmetrize=True)
+    u, base = gg.disjoint_union([a, b])
+    assert base.tolist() == [0, 3, 5] and u.n == 5 and u.m == a.m + b.m
+    assert u.indices[u.offsets[3]:u.offsets[4]].tolist() == [4]
+    assert u.weights[u.offsets[3]:u.offsets[4]].tolist() == [7]
+    assert u.offsets[:4].tolist() == a.offsets.tolist()
