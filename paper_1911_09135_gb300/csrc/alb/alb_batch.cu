@@ -41,7 +41,10 @@ __device__ __forceinline__ uint32_t act_mask(const BatchAux* x, uint32_t r, uint
 // OR `bits` into the entry for round `tag`; true if the entry had no bit of that round before
 // (the caller then appends the vertex to the next frontier exactly once).
 __device__ __forceinline__ bool act_or(unsigned long long* p, uint32_t tag, uint32_t bits) {
-  unsigned long long old = *(volatile unsigned long long*)p, assumed;
+  // A cached read may be stale, but an entry only gains bits within a round: if it already
+  // holds all of `bits` for this round they are really there; otherwise the CAS below
+  // corrects a stale guess.
+  unsigned long long old = *p, assumed;
   do {
     assumed = old;
     const uint32_t ot = (uint32_t)(assumed >> 32), om = (uint32_t)assumed;
@@ -87,12 +90,20 @@ struct MsSsspOp {
     const uint32_t* ru = x->lab + (size_t)v * 32u;
     uint32_t* rd = x->lab + (size_t)dst * 32u;
     uint32_t nb = 0u;
-    for (uint32_t b = M; b; b &= b - 1u) {
-      const uint32_t s = __ffs(b) - 1;
-      const uint32_t du = ru[s];
-      if ((uint64_t)du + w < (uint64_t)rd[s]) {
-        atomicMin(rd + s, du + w);
-        nb |= 1u << s;
+    // two sources per step, their four label loads issued together
+    for (uint32_t b = M; b;) {
+      const uint32_t s0 = __ffs(b) - 1;
+      b &= b - 1u;
+      const uint32_t s1 = b ? __ffs(b) - 1 : s0;
+      b &= b - 1u;
+      const uint32_t du0 = ru[s0], dv0 = rd[s0], du1 = ru[s1], dv1 = rd[s1];
+      if ((uint64_t)du0 + w < (uint64_t)dv0) {
+        atomicMin(rd + s0, du0 + w);
+        nb |= 1u << s0;
+      }
+      if (s1 != s0 && (uint64_t)du1 + w < (uint64_t)dv1) {
+        atomicMin(rd + s1, du1 + w);
+        nb |= 1u << s1;
       }
     }
     return nb && act_or(act_of(x, a.next) + dst, a.next, nb);
