@@ -59,7 +59,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["alb", "reference"], default="alb")
     ap.add_argument("--workload", choices=["rmat24-hubs", "rmat22-hubs", "rmat22", "rmat16",
-                                           "batch-sources", "batch-graphs"],
+                                           "batch-sources", "batch-graphs", "ablation"],
                     default="rmat24-hubs",
                     help="batch-*: batched vs one-query-at-a-time throughput (separate line)")
     ap.add_argument("--apps", default="", help="comma list restricting the workload's apps")
@@ -559,6 +559,7 @@ def batch_arm(args, dist):
         n = g.n
         for app, single, batch in (("bfs", alb.alb_bfs, alb.alb_bfs_batch),
                                    ("sssp", alb.alb_sssp, alb.alb_sssp_batch)):
+            tuned, _ = G.autotune(app, int(srcs[0]), reps=2)  # applies to both paths below
             def plain():
                 for i, s in enumerate(srcs.tolist()):
                     single(G.h, s, out[i * n:(i + 1) * n])
@@ -566,6 +567,8 @@ def batch_arm(args, dist):
             ms_batch = timed(lambda: batch(G.h, d_srcs, 128, out), args.steps)
             res[app] = {"queries": 128, "ms_plain": round(ms_plain, 3), "ms_batched": round(ms_batch, 3),
                         "speedup": round(ms_plain / ms_batch, 2),
+                        "autotuned": {"hub_threshold": tuned.hub_threshold, "twc_cta_min": tuned.twc_cta_min,
+                                      "twc_warp_min": tuned.twc_warp_min},
                         "queries_per_s_batched": round(128 / (ms_batch * 1e-3), 1)}
         G.close()
         desc = "128 sources (seed 4) on rmat22-sym (scale 22, ef 16, seed 2, w in [1,100])"
@@ -605,9 +608,64 @@ def batch_arm(args, dist):
         print(json.dumps(line), flush=True)
 
 
+def ablation_arm(args, dist):
+    """The paper's load-balancing comparison (Sec. 5.1, Table 2; Fig. 5; the threshold study)
+    on the severe-imbalance graph: per-app device time under
+      alb        - default ALB: threshold = LB threads, cyclic distribution
+      alb-blocked- ALB with the blocked distribution (Sec. 4.1)
+      twc        - threshold above the maximum degree: TWC only, the LB kernel never runs
+      lb-all     - threshold 0: every active vertex goes to the LB kernel (LB for all)
+      t=2^k      - the threshold sweep."""
+    import torch
+    from paper_1911_09135_gb300 import alb
+
+    torch.cuda.set_device(dist.local)
+    alb.load()
+    g, desc, apps = workload("rmat24-hubs")
+    step = GpuStep(g, apps, alb, torch)
+    stream = torch.cuda.current_stream()
+    settings = [("alb", {}), ("alb-blocked", {"distribution": 1}), ("twc", {"hub_threshold": 1 << 40}),
+                ("lb-all", {"hub_threshold": 0})]
+    settings += [(f"t=2^{k}", {"hub_threshold": 1 << k}) for k in (8, 10, 12, 14, 16, 18, 20)]
+    base = step.G.params()
+    table = {}
+    for name, kw in settings:
+        step.G.set_params(**{**{"hub_threshold": base.hub_threshold, "distribution": 0}, **kw})
+        row = {}
+        for a in apps:
+            step.run_app(a)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                step.run_app(a)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            st = step.G.stats()
+            row[a] = {"ms": round(e0.elapsed_time(e1) / args.steps, 3), "lb_rounds": st["hub_rounds"]}
+        table[name] = row
+    step.close()
+    line = {"metric": "per-app device time (ms) by load-balancing policy", "unit": "ms",
+            "higher_is_better": False, "n_gpus": dist.world, "steps": args.steps,
+            "config": {"workload": f"{g.name}: {desc}",
+                       "default_threshold": "threads of the LB kernel (alb_params.hub_threshold = -1)"},
+            "table": table}
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     dist = Dist()
+    if args.workload == "ablation":
+        import torch
+        dist.init("nccl" if torch.cuda.is_available() else "gloo")
+        try:
+            ablation_arm(args, dist)
+        finally:
+            dist.done()
+        return
     if args.workload.startswith("batch-"):
         import torch
         dist.init("nccl" if torch.cuda.is_available() else "gloo")

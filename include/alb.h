@@ -181,6 +181,27 @@ alb_status alb_bfs_multi(alb_graph g, const uint32_t* hd_srcs, uint32_t k, uint3
 alb_status alb_sssp_multi(alb_graph g, const uint32_t* hd_srcs, uint32_t k, uint32_t* hd_dist,
                           alb_stream stream);
 
+/* -------------------------------------------------------------- autotuner */
+
+typedef enum {
+  ALB_APP_BFS = 0,
+  ALB_APP_SSSP = 1,
+  ALB_APP_CC = 2,
+  ALB_APP_PAGERANK = 3, /* d = 0.85, tol = 1e-6 */
+  ALB_APP_KCORE = 4     /* k = 32 */
+} alb_app;
+
+/* Pick the load-balancing knobs for one application on this graph by timing it on the device
+ * (Sec. 4.1 "Threshold": the best threshold depends on the hardware; Sec. 5.1 finds a wide
+ * flat range). Coordinate search: the threshold over {threads of the LB kernel, 2^8, 2^10, ...,
+ * 2^20, never huge}, then twc_cta_min in {128, 256, 512, 1024} x twc_warp_min in {16, 32, 64}
+ * at the best threshold; each setting is timed as the mean of `reps` calls after one warm-up
+ * call. The fastest setting is applied to the handle and returned in *best (may be NULL) with
+ * its time in *best_ms (may be NULL). src is used by bfs and sssp. Synchronises `stream`.
+ * Results of every setting are identical (only the schedule changes). */
+alb_status alb_autotune(alb_graph g, alb_app app, uint32_t src, uint32_t reps, alb_params* best,
+                        float* best_ms, alb_stream stream);
+
 /* ------------------------------------------------------------ diagnostics */
 
 /* Algorithm 1 alone, on the device, for an explicit worklist hd_wl[nf]:

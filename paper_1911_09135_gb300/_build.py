@@ -29,6 +29,7 @@ ALB_SOURCES = [
     "alb/alb_traverse.cu",
     "alb/alb_pagerank.cu",
     "alb/alb_batch.cu",
+    "alb/alb_tune.cu",
 ]
 ALB_HEADERS = [
     "alb/alb_internal.cuh",

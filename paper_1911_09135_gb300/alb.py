@@ -33,8 +33,10 @@ EXPORTS = [
     "alb_get_params", "alb_bfs", "alb_sssp", "alb_cc", "alb_pagerank", "alb_kcore",
     "alb_bfs_batch", "alb_sssp_batch", "alb_inspect", "alb_lb_trace", "alb_threshold_rule",
     "alb_sync", "alb_get_stats", "alb_status_str", "alb_version", "alb_bfs_noalloc",
-    "alb_bfs_multi", "alb_sssp_multi",
+    "alb_bfs_multi", "alb_sssp_multi", "alb_autotune",
 ]
+
+ALB_APP = {"bfs": 0, "sssp": 1, "cc": 2, "pr": 3, "pagerank": 3, "kcore": 4}
 
 
 class AlbError(RuntimeError):
@@ -109,6 +111,7 @@ def load(build_if_missing: bool = False):
         "alb_bfs_batch": ([_P, _P, _U32, _P, _P], S),
         "alb_sssp_batch": ([_P, _P, _U32, _P, _P], S),
         "alb_bfs_multi": ([_P, _P, _U32, _P, _P], S),
+        "alb_autotune": ([_P, S, _U32, _U32, ctypes.POINTER(alb_params), ctypes.POINTER(ctypes.c_float), _P], S),
         "alb_sssp_multi": ([_P, _P, _U32, _P, _P], S),
         "alb_inspect": ([_P, _P, _U32, _P, _P, _P, _P, _P], S),
         "alb_lb_trace": ([_P, _P, _P, _U32, _P, _P, _P, _P], S),
@@ -249,6 +252,16 @@ def alb_bfs_multi(g, srcs, k, levels, stream=None) -> None:
 
 def alb_sssp_multi(g, srcs, k, dist, stream=None) -> None:
     _check(load().alb_sssp_multi(g, _ptr(srcs), k, _ptr(dist), _stream(stream)), "alb_sssp_multi")
+
+
+def alb_autotune(g, app, src=0, reps=3, stream=None):
+    """Returns (best alb_params, best time in ms); the best setting is left applied."""
+    p = alb_params()
+    ms = ctypes.c_float(0.0)
+    code = ALB_APP[app] if isinstance(app, str) else int(app)
+    _check(load().alb_autotune(g, code, src, reps, ctypes.byref(p), ctypes.byref(ms), _stream(stream)),
+           "alb_autotune")
+    return p, float(ms.value)
 
 
 def alb_inspect(g, wl, nf, bins, work, prefix, counts, stream=None) -> None:
@@ -399,6 +412,9 @@ class Graph:
         out = self._out(out, np.uint32)
         alb_sssp_multi(self.h, srcs, _numel(srcs), out, stream)
         return out
+
+    def autotune(self, app, src=0, reps=3, stream=None):
+        return alb_autotune(self.h, app, src, reps, stream)
 
     def inspect(self, worklist, stream=None):
         wl = np.ascontiguousarray(worklist, dtype=np.uint32)

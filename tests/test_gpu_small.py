@@ -369,3 +369,21 @@ def test_batch_argument_errors(rmat13):
     with pytest.raises(alb.AlbError):
         G.bfs_multi(np.array([g.n + 5], dtype=np.uint32))
     G.close()
+
+
+@pytest.mark.parametrize("app", ["bfs", "sssp", "cc", "pr", "kcore"])
+def test_autotune_keeps_results_exact(rmat13, app):
+    g = rmat13
+    G = make(g)
+    src = g.max_degree_vertex()
+    p, ms = G.autotune(app, src, reps=2)
+    assert ms > 0
+    assert p.hub_threshold in [-1, 1 << 40] + [1 << k for k in range(8, 21, 2)]
+    assert p.twc_cta_min in (128, 256, 512, 1024) and p.twc_warp_min in (16, 32, 64)
+    q = G.params()
+    assert (q.hub_threshold, q.twc_cta_min, q.twc_warp_min) == (p.hub_threshold, p.twc_cta_min, p.twc_warp_min)
+    got = run_all(G, g, src, k=32)
+    ref = oracle_all(g, src, k=32)
+    for a in ref:
+        assert np.array_equal(got[a], ref[a]), a
+    G.close()
