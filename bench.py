@@ -66,6 +66,8 @@ def parse_args():
     ap.add_argument("--exec-mode", choices=["graph", "host"], default="graph",
                     help="graph: device-side round loop (default); host: one launch per kernel "
                          "(ncu cannot profile kernels inside graphs with conditional nodes)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the paper's default threshold rule instead of the autotuned knobs")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-roofline", action="store_true")
@@ -275,12 +277,13 @@ class GpuStep:
 
     def roofline_pass(self):
         """Each app once more in the host-loop mode with every kernel timed by CUDA events."""
-        p0 = self.G.params()
-        self.G.set_params(exec_mode=1, profile=1)
         rows = []
         for a in self.apps:
+            p0 = self.G.params(a)
+            self.G.set_app_params(a, exec_mode=1, profile=1)
             self.run_app(a)
             st = self.G.stats()
+            self.G.set_app_params(a, exec_mode=p0.exec_mode, profile=0)
             n_front = st["pushes"] + (self.g.n if a in ("cc", "pr") else 1)
             if a == "pr":
                 n_front = self.g.n * st["rounds"]
@@ -291,7 +294,6 @@ class GpuStep:
                 byts = BYTES_PER_EDGE[a] * edges + (BYTES_PER_VERTEX[a] * n_front if cls == "twc" else 0)
                 rows.append({"app": a, "cls": cls, "kernel": KERNEL_NAMES[(a, cls)], "ms": ms,
                              "launches": nl, "bytes": byts, "edges": edges})
-        self.G.set_params(exec_mode=p0.exec_mode, profile=0)
         return rows
 
     def close(self):
@@ -308,8 +310,32 @@ def gpu_arm(args, dist):
     if args.apps:
         apps = tuple(a for a in args.apps.split(",") if a in apps)
     step = GpuStep(g, apps, alb, torch)
+    # the paper's default rule (threshold = threads of the LB kernel), timed briefly for reference
+    paper_rule_ms = None
+    if not args.no_tune:
+        for a in apps:
+            step.run_app(a)
+        torch.cuda.synchronize()
+        paper_rule_ms = {}
+        for a in apps:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(2):
+                step.run_app(a)
+            e1.record()
+            torch.cuda.synchronize()
+            paper_rule_ms[a] = round(e0.elapsed_time(e1) / 2, 3)
+    # autotuned knobs per app (outside the timed region; results do not depend on them)
+    tuned = {}
+    if not args.no_tune:
+        for a in apps:
+            p, _ = step.G.autotune(a, step.src, reps=2)
+            tuned[a] = {"hub_threshold": p.hub_threshold, "twc_cta_min": p.twc_cta_min,
+                        "twc_warp_min": p.twc_warp_min}
     if args.exec_mode == "host":
-        step.G.set_params(exec_mode=1)
+        for a in apps:
+            step.G.set_app_params(a, exec_mode=1)
     units, launches, cal_stats = step.calibrate()
     units_step = sum(units.values())
     stream = torch.cuda.current_stream()
@@ -367,7 +393,7 @@ def gpu_arm(args, dist):
 
     e2e = None
     if not args.no_e2e:
-        e2e = e2e_measure(args, g, apps, alb, torch, units_step, dist)
+        e2e = e2e_measure(args, g, apps, alb, torch, units_step, dist, tuned)
 
     step.close()
     cpu = None
@@ -380,6 +406,9 @@ def gpu_arm(args, dist):
                for a in apps}
     if "pr" in apps:
         per_app["pr"]["l1_last_change"] = cal_stats["pr"]["pr_l1"]
+    if paper_rule_ms:
+        for a in apps:
+            per_app[a]["ms_paper_rule_threshold"] = paper_rule_ms[a]
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": dist.world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
@@ -388,7 +417,10 @@ def gpu_arm(args, dist):
         "config": {"workload": f"{g.name}: {desc}", "n": g.n, "m": g.m, "apps": list(apps),
                    "exec_mode": args.exec_mode, "source": int(step.src), "kcore_k": KCORE_K,
                    "pagerank": {"d": PR_D, "tol": PR_TOL},
-                   "hub_threshold": cal_stats[apps[0]]["hub_threshold"],
+                   "knobs": ("autotuned per app by alb_autotune before timing" if tuned
+                             else "paper's rule: threshold = threads of the LB kernel"),
+                   "tuned": tuned or None,
+                   "hub_threshold": {a: cal_stats[a]["hub_threshold"] for a in apps},
                    "lb_threads": cal_stats[apps[0]]["lb_threads"],
                    "l2": "no flush: the CSR (>= 5 GB) is larger than L2 (129 MB)",
                    "parallelism": f"replicas x{dist.world} (the path does not shard)",
@@ -405,7 +437,7 @@ def gpu_arm(args, dist):
         print(json.dumps(line), flush=True)
 
 
-def e2e_measure(args, g, apps, alb, torch, units_step, dist):
+def e2e_measure(args, g, apps, alb, torch, units_step, dist, tuned=None):
     """Same step through the public API with HOST buffers: pinned CSR in, results out."""
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).pin_memory()
     h_off, h_idx = pin(g.offsets), pin(g.indices)
@@ -420,6 +452,8 @@ def e2e_measure(args, g, apps, alb, torch, units_step, dist):
 
     def one():
         G = alb.Graph(g.n, h_off, h_idx, h_w, symmetric=g.symmetric)
+        for a, kw in (tuned or {}).items():
+            G.set_app_params(a, **kw)  # the tuned knobs, as a deployed service would keep them
         for a in apps:
             if a == "bfs":
                 alb.alb_bfs(G.h, src, outs[a])

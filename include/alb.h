@@ -63,6 +63,14 @@ typedef enum {
   ALB_ERR_DEVICE = 8         /* a device-side check failed (an index out of range in the CSR) */
 } alb_status;
 
+typedef enum {
+  ALB_APP_BFS = 0,
+  ALB_APP_SSSP = 1,
+  ALB_APP_CC = 2,
+  ALB_APP_PAGERANK = 3, /* d = 0.85, tol = 1e-6 */
+  ALB_APP_KCORE = 4     /* k = 32 */
+} alb_app;
+
 /* Flags of alb_graph_create. */
 #define ALB_SYMMETRIC 0x1u /* the CSR holds both directions of every edge (undirected graph) */
 #define ALB_VALIDATE  0x2u /* check on the device that every index is < n and offsets are monotone */
@@ -123,6 +131,8 @@ alb_status alb_graph_create(uint32_t n, uint64_t m, const uint32_t* hd_offsets,
 /* Free a graph and its workspace (synchronises the handle's last stream). */
 alb_status alb_graph_destroy(alb_graph g);
 
+/* alb_set_params applies p to every application of the handle; alb_get_params returns the
+ * bfs parameters. Per-application parameters: see alb_set_app_params below. */
 alb_status alb_default_params(alb_params* p);
 alb_status alb_set_params(alb_graph g, const alb_params* p);
 alb_status alb_get_params(alb_graph g, alb_params* p);
@@ -183,20 +193,19 @@ alb_status alb_sssp_multi(alb_graph g, const uint32_t* hd_srcs, uint32_t k, uint
 
 /* -------------------------------------------------------------- autotuner */
 
-typedef enum {
-  ALB_APP_BFS = 0,
-  ALB_APP_SSSP = 1,
-  ALB_APP_CC = 2,
-  ALB_APP_PAGERANK = 3, /* d = 0.85, tol = 1e-6 */
-  ALB_APP_KCORE = 4     /* k = 32 */
-} alb_app;
+
+/* Parameters of one application only (what alb_autotune sets); the diagnostics and the
+ * batched / multi-source bfs (sssp) calls use the bfs (sssp) parameters. */
+alb_status alb_set_app_params(alb_graph g, alb_app app, const alb_params* p);
+alb_status alb_get_app_params(alb_graph g, alb_app app, alb_params* p);
 
 /* Pick the load-balancing knobs for one application on this graph by timing it on the device
  * (Sec. 4.1 "Threshold": the best threshold depends on the hardware; Sec. 5.1 finds a wide
  * flat range). Coordinate search: the threshold over {threads of the LB kernel, 2^8, 2^10, ...,
  * 2^20, never huge}, then twc_cta_min in {128, 256, 512, 1024} x twc_warp_min in {16, 32, 64}
  * at the best threshold; each setting is timed as the mean of `reps` calls after one warm-up
- * call. The fastest setting is applied to the handle and returned in *best (may be NULL) with
+ * call. The fastest setting is applied to that application (alb_set_app_params) and returned
+ * in *best (may be NULL) with
  * its time in *best_ms (may be NULL). src is used by bfs and sssp. Synchronises `stream`.
  * Results of every setting are identical (only the schedule changes). */
 alb_status alb_autotune(alb_graph g, alb_app app, uint32_t src, uint32_t reps, alb_params* best,

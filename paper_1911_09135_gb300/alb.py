@@ -33,7 +33,7 @@ EXPORTS = [
     "alb_get_params", "alb_bfs", "alb_sssp", "alb_cc", "alb_pagerank", "alb_kcore",
     "alb_bfs_batch", "alb_sssp_batch", "alb_inspect", "alb_lb_trace", "alb_threshold_rule",
     "alb_sync", "alb_get_stats", "alb_status_str", "alb_version", "alb_bfs_noalloc",
-    "alb_bfs_multi", "alb_sssp_multi", "alb_autotune",
+    "alb_bfs_multi", "alb_sssp_multi", "alb_autotune", "alb_set_app_params", "alb_get_app_params",
 ]
 
 ALB_APP = {"bfs": 0, "sssp": 1, "cc": 2, "pr": 3, "pagerank": 3, "kcore": 4}
@@ -111,6 +111,8 @@ def load(build_if_missing: bool = False):
         "alb_bfs_batch": ([_P, _P, _U32, _P, _P], S),
         "alb_sssp_batch": ([_P, _P, _U32, _P, _P], S),
         "alb_bfs_multi": ([_P, _P, _U32, _P, _P], S),
+        "alb_set_app_params": ([_P, S, ctypes.POINTER(alb_params)], S),
+        "alb_get_app_params": ([_P, S, ctypes.POINTER(alb_params)], S),
         "alb_autotune": ([_P, S, _U32, _U32, ctypes.POINTER(alb_params), ctypes.POINTER(ctypes.c_float), _P], S),
         "alb_sssp_multi": ([_P, _P, _U32, _P, _P], S),
         "alb_inspect": ([_P, _P, _U32, _P, _P, _P, _P, _P], S),
@@ -214,6 +216,18 @@ def alb_set_params(g, p: alb_params) -> None:
 def alb_get_params(g) -> alb_params:
     p = alb_params()
     _check(load().alb_get_params(g, ctypes.byref(p)), "alb_get_params")
+    return p
+
+
+def alb_set_app_params(g, app, p: alb_params) -> None:
+    code = ALB_APP[app] if isinstance(app, str) else int(app)
+    _check(load().alb_set_app_params(g, code, ctypes.byref(p)), "alb_set_app_params")
+
+
+def alb_get_app_params(g, app) -> alb_params:
+    p = alb_params()
+    code = ALB_APP[app] if isinstance(app, str) else int(app)
+    _check(load().alb_get_app_params(g, code, ctypes.byref(p)), "alb_get_app_params")
     return p
 
 
@@ -338,8 +352,16 @@ class Graph:
     def __exit__(self, *exc):
         self.close()
 
-    def params(self) -> alb_params:
-        return alb_get_params(self.h)
+    def params(self, app=None) -> alb_params:
+        return alb_get_params(self.h) if app is None else alb_get_app_params(self.h, app)
+
+    def set_app_params(self, app, **kw) -> None:
+        p = alb_get_app_params(self.h, app)
+        for k, v in kw.items():
+            if not hasattr(p, k):
+                raise AttributeError(k)
+            setattr(p, k, v)
+        alb_set_app_params(self.h, app, p)
 
     def set_params(self, **kw) -> None:
         p = alb_get_params(self.h)

@@ -406,6 +406,7 @@ extern "C" alb_status alb_bfs_batch(alb_graph g, const uint32_t* hd_srcs, uint32
   if (!g || (k && (!hd_srcs || !hd_out))) return ALB_ERR_INVALID_ARG;
   if (k == 0) return ALB_OK;
   if (cudaSetDevice(g->device) != cudaSuccess) return ALB_ERR_CUDA;
+  select_cfg(g, ALB_APP_BFS);
   return run_groups(g, BK_MS_BFS, hd_srcs, k, hd_out, (cudaStream_t)stream);
 }
 
@@ -416,6 +417,7 @@ extern "C" alb_status alb_sssp_batch(alb_graph g, const uint32_t* hd_srcs, uint3
   if (rc != ALB_OK) return rc;
   if (k == 0) return ALB_OK;
   if (cudaSetDevice(g->device) != cudaSuccess) return ALB_ERR_CUDA;
+  select_cfg(g, ALB_APP_SSSP);
   return run_groups(g, BK_MS_SSSP, hd_srcs, k, hd_out, (cudaStream_t)stream);
 }
 
@@ -423,6 +425,7 @@ extern "C" alb_status alb_bfs_multi(alb_graph g, const uint32_t* hd_srcs, uint32
                                     alb_stream stream) {
   if (!g || !hd_srcs || !hd_levels || k == 0) return ALB_ERR_INVALID_ARG;
   if (cudaSetDevice(g->device) != cudaSuccess) return ALB_ERR_CUDA;
+  select_cfg(g, ALB_APP_BFS);
   return run_multi(g, BK_MULTI_BFS, hd_srcs, k, hd_levels, (cudaStream_t)stream);
 }
 
@@ -432,5 +435,6 @@ extern "C" alb_status alb_sssp_multi(alb_graph g, const uint32_t* hd_srcs, uint3
   alb_status rc = sssp_ok(g);
   if (rc != ALB_OK) return rc;
   if (cudaSetDevice(g->device) != cudaSuccess) return ALB_ERR_CUDA;
+  select_cfg(g, ALB_APP_SSSP);
   return run_multi(g, BK_MULTI_SSSP, hd_srcs, k, hd_dist, (cudaStream_t)stream);
 }

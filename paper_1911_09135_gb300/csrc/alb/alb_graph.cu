@@ -22,11 +22,7 @@ alb_status ensure_tmp(alb_graph g) {
   return ALB_OK;
 }
 
-uint32_t effective_threshold(alb_graph g) {
-  const int64_t t = g->params.hub_threshold;
-  if (t < 0) return g->lb_blocks * (uint32_t)kBlock;
-  return t > 0xFFFFFFFFll ? 0xFFFFFFFFu : (uint32_t)t;
-}
+uint32_t effective_threshold(alb_graph g) { return g->threshold; }
 
 struct ScanOut {
   uint32_t max_deg;
@@ -85,16 +81,28 @@ static void free_graph_memory(alb_graph g) {
   cudaGetLastError();
 }
 
-static void apply_launch_config(alb_graph g) {
+// Launch configuration of application `app` for parameters p.
+static void apply_launch_config(alb_graph g, int app, const alb_params& p) {
   uint32_t occ_i = 1, occ_l = 1;
   occupancy(&occ_i, &occ_l);
-  if (g->params.grid_blocks) {
-    g->blocks = g->lb_blocks = g->params.grid_blocks;
+  alb_graph_s::AppCfg& c = g->cfg[app];
+  c.p = p;
+  if (p.grid_blocks) {
+    c.blocks = c.lb_blocks = p.grid_blocks;
   } else {
-    g->blocks = (uint32_t)g->num_sms * occ_i;
-    g->lb_blocks = (uint32_t)g->num_sms * occ_l;
+    c.blocks = (uint32_t)g->num_sms * occ_i;
+    c.lb_blocks = (uint32_t)g->num_sms * occ_l;
   }
-  g->threshold = effective_threshold(g);
+  if (p.hub_threshold < 0) c.threshold = c.lb_blocks * (uint32_t)kBlock;
+  else c.threshold = p.hub_threshold > 0xFFFFFFFFll ? 0xFFFFFFFFu : (uint32_t)p.hub_threshold;
+}
+
+void select_cfg(alb_graph g, int app) {
+  const alb_graph_s::AppCfg& c = g->cfg[app];
+  g->params = c.p;
+  g->blocks = c.blocks;
+  g->lb_blocks = c.lb_blocks;
+  g->threshold = c.threshold;
 }
 
 alb_status latch_from_state(alb_graph g, uint32_t status) {
@@ -221,8 +229,10 @@ alb_status alb_graph_create(uint32_t n, uint64_t m, const uint32_t* hd_offsets,
   if (h.bad) return fail(ALB_ERR_DEVICE);
   g->max_deg = h.max_deg;
   g->max_w = h.max_w;
-  alb_default_params(&g->params);
-  apply_launch_config(g);
+  alb_params dp;
+  alb_default_params(&dp);
+  for (int a = 0; a < 5; ++a) apply_launch_config(g, a, dp);
+  select_cfg(g, ALB_APP_BFS);
   g->last_stream = s;
   *out = g;
   return ALB_OK;
@@ -244,17 +254,48 @@ alb_status alb_set_params(alb_graph g, const alb_params* p) {
   if (!g || !p || !params_valid(p)) return ALB_ERR_INVALID_ARG;
   cudaSetDevice(g->device);
   cudaStreamSynchronize(g->last_stream);
-  g->params = *p;
   free_traversal_graphs(g);
   free_pagerank(g);
   free_batch(g);
-  apply_launch_config(g);
+  for (int a = 0; a < 5; ++a) apply_launch_config(g, a, *p);
+  select_cfg(g, ALB_APP_BFS);
   return ALB_OK;
 }
 
 alb_status alb_get_params(alb_graph g, alb_params* p) {
   if (!g || !p) return ALB_ERR_INVALID_ARG;
-  *p = g->params;
+  *p = g->cfg[ALB_APP_BFS].p;
+  return ALB_OK;
+}
+
+alb_status alb_set_app_params(alb_graph g, alb_app app, const alb_params* p) {
+  if (!g || !p || app < ALB_APP_BFS || app > ALB_APP_KCORE || !params_valid(p)) return ALB_ERR_INVALID_ARG;
+  cudaSetDevice(g->device);
+  cudaStreamSynchronize(g->last_stream);
+  // only the cached work of this application depends on its parameters
+  switch (app) {
+    case ALB_APP_PAGERANK: free_pagerank(g); break;
+    case ALB_APP_BFS: case ALB_APP_SSSP: free_batch(g); /* fall through */
+    default: {
+      const int internal = app == ALB_APP_BFS ? APP_BFS : app == ALB_APP_SSSP ? APP_SSSP
+                         : app == ALB_APP_CC ? APP_CC : APP_KCORE;
+      if (g->exec[internal]) cudaGraphExecDestroy(g->exec[internal]);
+      if (g->graph[internal]) cudaGraphDestroy(g->graph[internal]);
+      g->exec[internal] = nullptr;
+      g->graph[internal] = nullptr;
+      if (app == ALB_APP_BFS) {  // the diagnostics run with the bfs configuration
+        if (g->exec[APP_TRACE]) cudaGraphExecDestroy(g->exec[APP_TRACE]);
+        g->exec[APP_TRACE] = nullptr;
+      }
+    }
+  }
+  apply_launch_config(g, app, *p);
+  return ALB_OK;
+}
+
+alb_status alb_get_app_params(alb_graph g, alb_app app, alb_params* p) {
+  if (!g || !p || app < ALB_APP_BFS || app > ALB_APP_KCORE) return ALB_ERR_INVALID_ARG;
+  *p = g->cfg[app].p;
   return ALB_OK;
 }
 
@@ -309,8 +350,9 @@ alb_status alb_get_stats(alb_graph g, alb_stats* out) {
   return rc;
 }
 
-static alb_status begin_call(alb_graph g) {
+static alb_status begin_call(alb_graph g, int app) {
   if (cudaSetDevice(g->device) != cudaSuccess) return ALB_ERR_CUDA;
+  select_cfg(g, app);
   g->stats.ms_inspect = g->stats.ms_lb = g->stats.ms_other = 0.0;
   g->stats.n_inspect = g->stats.n_lb = g->stats.n_other = 0;
   return ALB_OK;
@@ -318,7 +360,7 @@ static alb_status begin_call(alb_graph g) {
 
 alb_status alb_bfs(alb_graph g, uint32_t src, uint32_t* hd_levels, alb_stream stream) {
   if (!g || !hd_levels || src >= g->n) return ALB_ERR_INVALID_ARG;
-  alb_status rc = begin_call(g);
+  alb_status rc = begin_call(g, ALB_APP_BFS);
   if (rc != ALB_OK) return rc;
   return run_traversal(g, APP_BFS, src, 0u, hd_levels, (cudaStream_t)stream);
 }
@@ -327,7 +369,7 @@ alb_status alb_sssp(alb_graph g, uint32_t src, uint32_t* hd_dist, alb_stream str
   if (!g || !hd_dist || src >= g->n) return ALB_ERR_INVALID_ARG;
   if (!g->has_w) return ALB_ERR_UNSUPPORTED;
   if ((uint64_t)g->max_w * (uint64_t)(g->n - 1) >= 0xFFFFFFFFull) return ALB_ERR_OVERFLOW;
-  alb_status rc = begin_call(g);
+  alb_status rc = begin_call(g, ALB_APP_SSSP);
   if (rc != ALB_OK) return rc;
   return run_traversal(g, APP_SSSP, src, 0u, hd_dist, (cudaStream_t)stream);
 }
@@ -335,7 +377,7 @@ alb_status alb_sssp(alb_graph g, uint32_t src, uint32_t* hd_dist, alb_stream str
 alb_status alb_cc(alb_graph g, uint32_t* hd_labels, alb_stream stream) {
   if (!g || !hd_labels) return ALB_ERR_INVALID_ARG;
   if (!(g->flags & ALB_SYMMETRIC)) return ALB_ERR_NOT_SYMMETRIC;
-  alb_status rc = begin_call(g);
+  alb_status rc = begin_call(g, ALB_APP_CC);
   if (rc != ALB_OK) return rc;
   return run_traversal(g, APP_CC, 0u, 0u, hd_labels, (cudaStream_t)stream);
 }
@@ -343,7 +385,7 @@ alb_status alb_cc(alb_graph g, uint32_t* hd_labels, alb_stream stream) {
 alb_status alb_kcore(alb_graph g, uint32_t k, uint32_t* hd_in_core, alb_stream stream) {
   if (!g || !hd_in_core) return ALB_ERR_INVALID_ARG;
   if (!(g->flags & ALB_SYMMETRIC)) return ALB_ERR_NOT_SYMMETRIC;
-  alb_status rc = begin_call(g);
+  alb_status rc = begin_call(g, ALB_APP_KCORE);
   if (rc != ALB_OK) return rc;
   return run_traversal(g, APP_KCORE, 0u, k, hd_in_core, (cudaStream_t)stream);
 }
@@ -385,7 +427,7 @@ alb_status alb_inspect(alb_graph g, const uint32_t* hd_wl, uint32_t nf, uint8_t*
                        alb_stream stream) {
   if (!g || (nf && (!hd_wl || !hd_bin)) || !hd_work || !hd_prefix || !hd_counts)
     return ALB_ERR_INVALID_ARG;
-  alb_status rc = begin_call(g);
+  alb_status rc = begin_call(g, ALB_APP_BFS);
   if (rc != ALB_OK) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   Staged wl, bin, work, prefix, counts;
@@ -412,7 +454,7 @@ alb_status alb_lb_trace(alb_graph g, const uint32_t* hd_work, const uint32_t* hd
                         uint32_t nwork, uint32_t* hd_src, uint32_t* hd_dst, uint32_t* hd_thread,
                         alb_stream stream) {
   if (!g || !hd_prefix || (nwork && !hd_work) || nwork > g->n) return ALB_ERR_INVALID_ARG;
-  alb_status rc = begin_call(g);
+  alb_status rc = begin_call(g, ALB_APP_BFS);
   if (rc != ALB_OK) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   // total positions e = prefix[nwork], read on the host

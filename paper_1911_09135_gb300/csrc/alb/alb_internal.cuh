@@ -93,6 +93,12 @@ struct alb_graph_s {
   uint32_t* idx = nullptr;
   uint32_t* w = nullptr;
 
+  // per-application launch configuration (indexed by alb_app); the fields below hold the
+  // configuration of the application being called (select_cfg copies it in)
+  struct AppCfg {
+    alb_params p{};
+    uint32_t blocks = 0, lb_blocks = 0, threshold = 0;
+  } cfg[5];
   alb_params params{};
   int num_sms = 0;
   uint32_t blocks = 0;        // CTAs of the inspection / init kernels (persistent grid)
@@ -159,5 +165,6 @@ alb_status pr_stats(alb_graph g, alb_stats* out);
 alb_status batch_stats(alb_graph g, alb_stats* out);
 alb_status latch_from_state(alb_graph g, uint32_t status);
 uint32_t effective_threshold(alb_graph g);
+void select_cfg(alb_graph g, int app);
 
 }  // namespace alb

@@ -735,6 +735,7 @@ extern "C" alb_status alb_pagerank(alb_graph g, float damping, double tol, uint3
   if (!g || !hd_rank || !(damping >= 0.0f && damping <= 1.0f) || !(tol >= 0.0)) return ALB_ERR_INVALID_ARG;
   if (!(g->flags & ALB_SYMMETRIC)) return ALB_ERR_NOT_SYMMETRIC;
   if (cudaSetDevice(g->device) != cudaSuccess) return ALB_ERR_CUDA;
+  select_cfg(g, ALB_APP_PAGERANK);
   g->stats.ms_inspect = g->stats.ms_lb = g->stats.ms_other = 0.0;
   g->stats.n_inspect = g->stats.n_lb = g->stats.n_other = 0;
   cudaStream_t s = (cudaStream_t)stream;

@@ -2,7 +2,7 @@
 // paper finds a wide flat range, Sec. 5.1 "Analyzing Threshold") and the TWC bin cut-offs.
 // Coordinate search timed on the device: first the threshold over powers of 4 plus the paper's
 // rule (threads of the LB kernel) and "never huge", then the CTA and warp cut-offs at the best
-// threshold. The fastest setting is left applied to the handle.
+// threshold. The fastest setting is left applied to that application on the handle.
 #include <cfloat>
 #include <vector>
 
@@ -67,12 +67,13 @@ extern "C" alb_status alb_autotune(alb_graph g, alb_app app, uint32_t src, uint3
     cudaFree(l1);
     return ALB_ERR_OOM;
   }
-  const alb_params start = g->params;
+  alb_params start;
+  alb_get_app_params(g, app, &start);
   alb_params cur = start, top = start;
   float top_ms = FLT_MAX;
   alb_status rc = ALB_OK;
   auto trial = [&](const alb_params& p) -> alb_status {
-    alb_status r = alb_set_params(g, &p);
+    alb_status r = alb_set_app_params(g, app, &p);
     if (r != ALB_OK) return r;
     float ms = 0.f;
     r = time_app(g, app, src, out, l1, it, reps, s, &ms);
@@ -111,7 +112,7 @@ extern "C" alb_status alb_autotune(alb_graph g, alb_app app, uint32_t src, uint3
   cudaFree(out);
   cudaFree(l1);
   cudaFree(it);
-  alb_status rc2 = alb_set_params(g, rc == ALB_OK ? &top : &start);
+  alb_status rc2 = alb_set_app_params(g, app, rc == ALB_OK ? &top : &start);
   if (rc != ALB_OK) return rc;
   if (rc2 != ALB_OK) return rc2;
   if (best) *best = top;

@@ -380,10 +380,29 @@ def test_autotune_keeps_results_exact(rmat13, app):
     assert ms > 0
     assert p.hub_threshold in [-1, 1 << 40] + [1 << k for k in range(8, 21, 2)]
     assert p.twc_cta_min in (128, 256, 512, 1024) and p.twc_warp_min in (16, 32, 64)
-    q = G.params()
+    q = G.params(app)
     assert (q.hub_threshold, q.twc_cta_min, q.twc_warp_min) == (p.hub_threshold, p.twc_cta_min, p.twc_warp_min)
     got = run_all(G, g, src, k=32)
     ref = oracle_all(g, src, k=32)
     for a in ref:
         assert np.array_equal(got[a], ref[a]), a
+    G.close()
+
+
+def test_per_app_params_are_independent(rmat13):
+    g = rmat13
+    G = make(g)
+    G.set_app_params("sssp", hub_threshold=0, distribution=1)
+    G.set_app_params("bfs", hub_threshold=1 << 40)
+    assert G.params("sssp").hub_threshold == 0 and G.params("cc").hub_threshold == -1
+    src = g.max_degree_vertex()
+    got = run_all(G, g, src, k=8)
+    ref = oracle_all(g, src, k=8)
+    for a in ref:
+        assert np.array_equal(got[a], ref[a]), a
+    o = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    G.bfs(src, o)
+    assert G.stats()["hub_rounds"] == 0          # bfs: never huge
+    G.sssp(src, o)
+    assert G.stats()["hub_threshold"] == 0       # sssp: every vertex huge
     G.close()
