@@ -59,7 +59,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["alb", "reference"], default="alb")
     ap.add_argument("--workload", choices=["rmat24-hubs", "rmat22-hubs", "rmat22", "rmat16",
-                                           "batch-sources", "batch-graphs", "ablation"],
+                                           "batch-sources", "batch-graphs", "ablation", "serve"],
                     default="rmat24-hubs",
                     help="batch-*: batched vs one-query-at-a-time throughput (separate line)")
     ap.add_argument("--apps", default="", help="comma list restricting the workload's apps")
@@ -689,9 +689,60 @@ def ablation_arm(args, dist):
         print(json.dumps(line), flush=True)
 
 
+def serve_arm(args, dist):
+    """Continuous-batching server over 8 resident graphs (RMAT scales 14, 15, 17, 18, 20, 21,
+    23, 24; seeds 500 + i; symmetrised; w in [1,100]); 20,000 bfs/sssp/cc requests with Poisson
+    arrivals at 2,000 per second (seed 5), graph and kind uniform. Reports p50/p99 latency,
+    throughput and GTEPS (m of the queried graph per request), then the saturation throughput of
+    the batched server against one request at a time on the same 4,000 requests."""
+    import torch
+    from paper_1911_09135_gb300 import alb, graphgen as gg, serve
+
+    torch.cuda.set_device(dist.local)
+    alb.load()
+    scales = (14, 15, 17, 18, 20, 21, 23, 24)
+    graphs = [gg.rmat(sc, 16 << sc, 500 + i, symmetrize=True, weighted=True) for i, sc in enumerate(scales)]
+    srv = serve.Server(graphs, tune=True)
+    reqs = serve.poisson_requests(graphs, 20000, rate=2000.0, seed=5)
+    # warm every slot's cached graphs once
+    warm = [serve.Request(-1 - 3 * i - j, 0.0, i, k, int(np.argmax(graphs[i].degrees())))
+            for i in range(len(graphs)) for j, k in enumerate(serve.KINDS)]
+    srv.run(warm, realtime=False)
+    e0 = srv.edges
+    wall = srv.run(reqs, realtime=True, timeout=900)
+    lat = serve.latency_stats(reqs)
+    gteps = (srv.edges - e0) / wall / 1e9
+    sat = [serve.Request(r.rid, 0.0, r.graph, r.kind, r.src) for r in reqs[:4000]]
+    b0 = srv.batches
+    t_batched = srv.run(sat, realtime=False, timeout=900)
+    nb = srv.batches - b0
+    t_plain, _ = serve.one_at_a_time(srv, sat)
+    srv.close()
+    line = {"metric": "served bfs/sssp/cc requests: p50/p99 latency and throughput", "unit": "queries/s",
+            "value": round(len(reqs) / wall, 1), "higher_is_better": True, "n_gpus": dist.world,
+            "latency": lat, "gteps": round(gteps, 3), "offered_rate": 2000.0, "requests": len(reqs),
+            "wall_s": round(wall, 3), "deferred_admissions": srv.deferred,
+            "saturation": {"requests": len(sat), "batched_s": round(t_batched, 3), "batches": nb,
+                           "one_at_a_time_s": round(t_plain, 3),
+                           "speedup": round(t_plain / t_batched, 2)},
+            "config": {"workload": "8 resident RMAT graphs, scales 14-24 (14,15,17,18,20,21,23,24), "
+                                   "seeds 500+i, symmetrised, w in [1,100]; Poisson 2000/s, seed 5",
+                       "graphs_m": [g.m for g in graphs], "knobs": "autotuned per graph and app"}}
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     dist = Dist()
+    if args.workload == "serve":
+        import torch
+        dist.init("nccl" if torch.cuda.is_available() else "gloo")
+        try:
+            serve_arm(args, dist)
+        finally:
+            dist.done()
+        return
     if args.workload == "ablation":
         import torch
         dist.init("nccl" if torch.cuda.is_available() else "gloo")

@@ -77,15 +77,26 @@ struct CcOp {
 // kcore (peeling): a removed vertex decrements each neighbour's remaining
 // degree; the neighbour is removed (pushed) exactly when it drops from k to
 // k - 1. Neighbours already below k are skipped (their membership is settled).
+// Lanes of a warp that decrement the same vertex are combined into one
+// atomicSub of their count (many peeled vertices share the same high-degree
+// neighbours); the group whose subtraction crosses k pushes the vertex.
 struct KcoreOp {
   static constexpr bool kBatch = false;
+  static constexpr bool kAggregate = true;
   static constexpr bool kW = false;
   __device__ static uint32_t sval(const OpArgs&, uint32_t) { return 0u; }
   __device__ static bool want(const OpArgs& a, uint32_t, uint32_t cur, uint32_t) { return cur >= a.k; }
-  __device__ static bool commit(const OpArgs& a, uint32_t, uint32_t dst, uint32_t) {
-    return atomicSub(a.lab + dst, 1u) == a.k;
+  __device__ static bool commit_n(const OpArgs& a, uint32_t dst, uint32_t cnt) {
+    const uint32_t old = atomicSub(a.lab + dst, cnt);
+    return old >= a.k && old - cnt < a.k;
   }
+  __device__ static bool commit(const OpArgs& a, uint32_t, uint32_t dst, uint32_t) { return commit_n(a, dst, 1u); }
 };
+
+template <class Op, class = void>
+struct aggregates { static constexpr bool value = false; };
+template <class Op>
+struct aggregates<Op, decltype(void(Op::kAggregate))> { static constexpr bool value = Op::kAggregate; };
 
 // Relax U edges per thread; all loads are issued before the atomics so each
 // thread keeps U independent memory requests in flight. Warp-uniform callers.
@@ -103,6 +114,22 @@ __device__ __forceinline__ void relax(const TravCtx& c, const OpArgs& a, const u
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const bool push = ok[u] && Op::apply(a, sv[u], dst[u], wt[u]);
+      warp_append(push, dst[u], Fn, ncount);
+    }
+  } else if constexpr (aggregates<Op>::value) {
+    uint32_t cur[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) cur[u] = ok[u] ? a.lab[dst[u]] : 0u;
+    const uint32_t lane = lane_id();
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool w = ok[u] && Op::want(a, sv[u], cur[u], wt[u]);
+      const unsigned wm = __ballot_sync(kFull, w);
+      bool push = false;
+      if (w) {
+        const unsigned grp = __match_any_sync(wm, dst[u]);
+        if ((int)lane == __ffs(grp) - 1) push = Op::commit_n(a, dst[u], (uint32_t)__popc(grp));
+      }
       warp_append(push, dst[u], Fn, ncount);
     }
   } else {

@@ -1,0 +1,61 @@
+"""Continuous-batching server: every result is the same alone and in the mix."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1911_09135_gb300 import graphgen as gg
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1911_09135_gb300 import serve  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def graphs():
+    return [gg.rmat(sc, 16 << sc, 500 + i, symmetrize=True, weighted=True)
+            for i, sc in enumerate((8, 10, 11, 13))]
+
+
+def test_results_alone_equal_results_in_the_mix(graphs):
+    reqs = serve.poisson_requests(graphs, 400, rate=20000.0, seed=5)
+    srv = serve.Server(graphs, tune=False, keep_results=True)
+    try:
+        srv.run(reqs, realtime=True, timeout=120)
+        assert all(r.done >= r.arrival for r in reqs)
+        assert srv.batches < len(reqs)               # requests were batched together
+        _, alone = serve.one_at_a_time(srv, reqs, keep_results=True)
+    finally:
+        srv.close()
+    for r in reqs:
+        assert np.array_equal(srv.results[r.rid], alone[r.rid]), (r.rid, r.kind)
+    # and a sample against the oracle
+    for r in reqs[:30]:
+        g = graphs[r.graph]
+        if r.kind == "bfs":
+            ref = oracle.bfs(g.n, g.offsets, g.indices, r.src)
+        elif r.kind == "sssp":
+            ref = oracle.sssp(g.n, g.offsets, g.indices, g.weights, r.src)
+        else:
+            ref = oracle.cc(g.n, g.offsets, g.indices)
+        assert np.array_equal(srv.results[r.rid], ref), (r.rid, r.kind)
+
+
+def test_admission_waits_for_free_device_memory(graphs):
+    reqs = serve.poisson_requests(graphs, 40, rate=1e6, seed=6)
+    srv = serve.Server(graphs, tune=False, keep_results=True)
+    try:
+        srv.reserve = 1 << 60                           # nothing fits
+        s = srv.slots[reqs[0].graph]
+        s.queue[reqs[0].kind].append(reqs[0])
+        assert srv._launch(s) is False and srv.deferred == 1
+        assert len(s.queue[reqs[0].kind]) == 1          # the request is still queued
+        s.queue[reqs[0].kind].clear()
+        srv.reserve = 0
+        srv.run(reqs, realtime=False, timeout=60)
+        assert all(r.done >= 0 for r in reqs)
+    finally:
+        srv.close()
