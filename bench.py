@@ -711,6 +711,7 @@ def serve_arm(args, dist):
     e0 = srv.edges
     wall = srv.run(reqs, realtime=True, timeout=900)
     lat = serve.latency_stats(reqs)
+    per_graph = serve.slot_stats(srv, reqs)
     gteps = (srv.edges - e0) / wall / 1e9
     sat = [serve.Request(r.rid, 0.0, r.graph, r.kind, r.src) for r in reqs[:4000]]
     b0 = srv.batches
@@ -721,7 +722,7 @@ def serve_arm(args, dist):
     line = {"metric": "served bfs/sssp/cc requests: p50/p99 latency and throughput", "unit": "queries/s",
             "value": round(len(reqs) / wall, 1), "higher_is_better": True, "n_gpus": dist.world,
             "latency": lat, "gteps": round(gteps, 3), "offered_rate": 2000.0, "requests": len(reqs),
-            "wall_s": round(wall, 3), "deferred_admissions": srv.deferred,
+            "wall_s": round(wall, 3), "deferred_admissions": srv.deferred, "per_graph": per_graph,
             "saturation": {"requests": len(sat), "batched_s": round(t_batched, 3), "batches": nb,
                            "one_at_a_time_s": round(t_plain, 3),
                            "speedup": round(t_plain / t_batched, 2)},

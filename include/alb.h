@@ -30,7 +30,10 @@
  *     output is host memory the library copies into it on the same stream.
  *   - Calls on one alb_graph must be ordered (same stream, or externally
  *     synchronised): a handle owns one workspace and is not thread-safe.
- *     Different handles are independent.
+ *     Different handles are independent. The first call of each kind on a
+ *     handle allocates its workspace and instantiates a CUDA graph, which can
+ *     wait for the whole device: make it (warm the handle) before running
+ *     several handles concurrently on different streams.
  *   - Argument errors are returned synchronously and enqueue nothing. Errors
  *     detected on the device (round limit exceeded, corrupt CSR) are latched in
  *     the handle and returned by alb_sync() and alb_get_stats().
@@ -128,11 +131,18 @@ alb_status alb_graph_create(uint32_t n, uint64_t m, const uint32_t* hd_offsets,
                             const uint32_t* hd_indices, const uint32_t* hd_weights,
                             uint32_t flags, alb_stream stream, alb_graph* out);
 
-/* Free a graph and its workspace (synchronises the handle's last stream). */
+/* A second handle on the same device graph: it shares the CSR (no copy) and the parameters
+ * of `src` at the time of the call, and owns a separate workspace, so calls on the two handles
+ * may run concurrently on different streams (e.g. several server slots on one large graph).
+ * The CSR is freed with the last handle that uses it. */
+alb_status alb_graph_clone(alb_graph src, alb_graph* out);
+
+/* Free a graph and its workspace (waits for the whole device first). */
 alb_status alb_graph_destroy(alb_graph g);
 
 /* alb_set_params applies p to every application of the handle; alb_get_params returns the
- * bfs parameters. Per-application parameters: see alb_set_app_params below. */
+ * bfs parameters. Per-application parameters: see alb_set_app_params below. Setting
+ * parameters drops cached work and waits for the whole device first. */
 alb_status alb_default_params(alb_params* p);
 alb_status alb_set_params(alb_graph g, const alb_params* p);
 alb_status alb_get_params(alb_graph g, alb_params* p);
@@ -175,7 +185,11 @@ alb_status alb_kcore(alb_graph g, uint32_t k, uint32_t* hd_in_core, alb_stream s
  * that share every CSR read: a frontier vertex carries the set of sources for which it is
  * active and each expanded edge is relaxed for all of them (bit-parallel for bfs). The
  * rounds use the same inspection, TWC and cyclic LB kernels (Algorithms 1 and 2). hd_srcs
- * has k entries (repeats allowed); each must be < n, else ALB_ERR_INVALID_ARG. Workspace:
+ * has k entries (repeats allowed); each must be < n: sources in host memory are checked at
+ * once (ALB_ERR_INVALID_ARG, nothing enqueued); sources in device memory are checked on the
+ * device, an invalid one is skipped and ALB_ERR_INVALID_ARG is returned by alb_sync. Sources
+ * in pinned host memory are copied asynchronously: keep them unchanged until the stream has
+ * passed the call. Workspace:
  * 32 labels + a mask and two tagged masks per vertex (148 bytes x n), allocated on first use. */
 alb_status alb_bfs_batch(alb_graph g, const uint32_t* hd_srcs, uint32_t k, uint32_t* hd_out,
                          alb_stream stream);
@@ -185,7 +199,7 @@ alb_status alb_sssp_batch(alb_graph g, const uint32_t* hd_srcs, uint32_t k, uint
 /* One traversal from a set of sources at distance 0: hd_levels[v] (hd_dist[v]) = distance from
  * the nearest of hd_srcs[0..k). On a graph that is the disjoint union of many graphs with one
  * source in each, this computes every graph's own bfs (sssp) in one launch sequence, which is
- * how many small graphs are batched. Each source must be < n. */
+ * how many small graphs are batched. Sources are checked as for alb_bfs_batch. */
 alb_status alb_bfs_multi(alb_graph g, const uint32_t* hd_srcs, uint32_t k, uint32_t* hd_levels,
                          alb_stream stream);
 alb_status alb_sssp_multi(alb_graph g, const uint32_t* hd_srcs, uint32_t k, uint32_t* hd_dist,
@@ -270,6 +284,15 @@ alb_status alb_get_stats(alb_graph g, alb_stats* out);
 
 /* Static string for a status code. */
 const char* alb_status_str(alb_status s);
+
+/* Bounds-checked build. libalb_checked.so (built with -DALB_CHECKED) tests every CSR, frontier,
+ * worklist and label-row index a round kernel uses; an index out of range is skipped and
+ * recorded instead of being accessed. alb_debug_check copies the handle's record (first
+ * failing code, its index and bound, number of failures; all zero when none failed, and
+ * always zero in the regular build) after synchronising the handle's last stream.
+ * alb_checked_build returns 1 in the checked build, 0 otherwise. */
+alb_status alb_debug_check(alb_graph g, uint32_t* out4);
+uint32_t alb_checked_build(void);
 
 /* Library version: major * 10000 + minor * 100 + patch. */
 uint32_t alb_version(void);

@@ -69,10 +69,14 @@ def build_graphgen(force: bool = False) -> str:
     return out
 
 
-def build_alb(force: bool = False, extra_flags: list[str] | None = None) -> str:
+def build_alb(force: bool = False, extra_flags: list[str] | None = None, checked: bool = False) -> str:
+    """libalb.so; checked=True builds libalb_checked.so (-DALB_CHECKED: bounds-checked kernels)."""
+    obj_dir = OBJ_DIR + ("_checked" if checked else "")
     os.makedirs(LIB_DIR, exist_ok=True)
-    os.makedirs(OBJ_DIR, exist_ok=True)
-    out = os.path.join(LIB_DIR, "libalb.so")
+    os.makedirs(obj_dir, exist_ok=True)
+    out = os.path.join(LIB_DIR, "libalb_checked.so" if checked else "libalb.so")
+    if checked:
+        extra_flags = list(extra_flags or []) + ["-DALB_CHECKED"]
     headers = [os.path.join(CSRC, h) for h in ALB_HEADERS] + [os.path.join(INCLUDE_DIR, "alb.h")]
     nvcc = _nvcc()
     flags = [
@@ -82,7 +86,7 @@ def build_alb(force: bool = False, extra_flags: list[str] | None = None) -> str:
 
     def compile_one(rel: str) -> str:
         src = os.path.join(CSRC, rel)
-        obj = os.path.join(OBJ_DIR, os.path.basename(rel) + ".o")
+        obj = os.path.join(obj_dir, os.path.basename(rel) + ".o")
         if force or not _newer(obj, [src] + headers + [__file__]):
             _run([nvcc, "-c", src, "-o", obj] + flags)
         return obj

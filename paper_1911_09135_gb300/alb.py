@@ -34,6 +34,7 @@ EXPORTS = [
     "alb_bfs_batch", "alb_sssp_batch", "alb_inspect", "alb_lb_trace", "alb_threshold_rule",
     "alb_sync", "alb_get_stats", "alb_status_str", "alb_version", "alb_bfs_noalloc",
     "alb_bfs_multi", "alb_sssp_multi", "alb_autotune", "alb_set_app_params", "alb_get_app_params",
+    "alb_graph_clone", "alb_debug_check", "alb_checked_build",
 ]
 
 ALB_APP = {"bfs": 0, "sssp": 1, "cc": 2, "pr": 3, "pagerank": 3, "kcore": 4}
@@ -82,7 +83,9 @@ _U32 = ctypes.c_uint32
 
 
 def lib_path() -> str:
-    return os.path.join(_build.LIB_DIR, "libalb.so")
+    """libalb.so, or the bounds-checked libalb_checked.so when ALB_CHECKED=1 is set."""
+    name = "libalb_checked.so" if os.environ.get("ALB_CHECKED") == "1" else "libalb.so"
+    return os.path.join(_build.LIB_DIR, name)
 
 
 def load(build_if_missing: bool = False):
@@ -93,13 +96,16 @@ def load(build_if_missing: bool = False):
     path = lib_path()
     if not os.path.exists(path):
         if not build_if_missing:
-            raise RuntimeError(f"libalb.so not found at {path}; run __graft_entry__.build()")
-        path = _build.build_alb()
+            raise RuntimeError(f"{path} not found; run __graft_entry__.build()")
+        path = _build.build_alb(checked=os.environ.get("ALB_CHECKED") == "1")
     lib = ctypes.CDLL(path)
     S = ctypes.c_int
     sig = {
         "alb_graph_create": ([_U32, ctypes.c_uint64, _P, _P, _P, _U32, _P, ctypes.POINTER(_P)], S),
         "alb_graph_destroy": ([_P], S),
+        "alb_graph_clone": ([_P, ctypes.POINTER(_P)], S),
+        "alb_debug_check": ([_P, _P], S),
+        "alb_checked_build": ([], _U32),
         "alb_default_params": ([ctypes.POINTER(alb_params)], S),
         "alb_set_params": ([_P, ctypes.POINTER(alb_params)], S),
         "alb_get_params": ([_P, ctypes.POINTER(alb_params)], S),
@@ -196,6 +202,12 @@ def alb_graph_create(n, m, offsets, indices, weights=None, flags=0, stream=None)
     h = _P()
     _check(lib.alb_graph_create(n, m, _ptr(offsets), _ptr(indices), _ptr(weights), flags,
                                 _stream(stream), ctypes.byref(h)), "alb_graph_create")
+    return h.value
+
+
+def alb_graph_clone(g) -> int:
+    h = _P()
+    _check(load().alb_graph_clone(g, ctypes.byref(h)), "alb_graph_clone")
     return h.value
 
 
@@ -310,6 +322,16 @@ def alb_version() -> int:
     return int(load().alb_version())
 
 
+def alb_checked_build() -> int:
+    return int(load().alb_checked_build())
+
+
+def alb_debug_check(g) -> list[int]:
+    out = np.zeros(4, dtype=np.uint32)
+    _check(load().alb_debug_check(g, out.ctypes.data), "alb_debug_check")
+    return out.tolist()
+
+
 ALB_NOALLOC_MAX_VERTICES = 1 << 20
 
 
@@ -330,6 +352,13 @@ class Graph:
         self.symmetric = symmetric
         flags = ALB_SYMMETRIC if symmetric else 0
         self.h = alb_graph_create(self.n, self.m, offsets, indices, weights, flags, stream)
+
+    def clone(self) -> "Graph":
+        """Another handle on the same device CSR with its own workspace (concurrent use)."""
+        c = Graph.__new__(Graph)
+        c.n, c.m, c.symmetric = self.n, self.m, self.symmetric
+        c.h = alb_graph_clone(self.h)
+        return c
 
     @classmethod
     def from_csr(cls, csr, stream=None):

@@ -65,6 +65,7 @@ struct MsBfsOp {
   }
   __device__ static bool apply(const OpArgs& a, uint32_t M, uint32_t dst, uint32_t) {
     const BatchAux* x = static_cast<const BatchAux*>(a.aux);
+    if (!ALB_IN_RANGE(a.chk, CHK_ROW, dst, a.n)) return false;
     uint32_t nw = M & ~x->seen[dst];
     if (!nw) return false;
     nw &= ~atomicOr(x->seen + dst, nw);
@@ -86,6 +87,7 @@ struct MsSsspOp {
   __device__ static uint32_t sval(const OpArgs&, uint32_t v) { return v; }
   __device__ static bool apply(const OpArgs& a, uint32_t v, uint32_t dst, uint32_t w) {
     const BatchAux* x = static_cast<const BatchAux*>(a.aux);
+    if (!ALB_IN_RANGE(a.chk, CHK_ROW, v, a.n) || !ALB_IN_RANGE(a.chk, CHK_ROW, dst, a.n)) return false;
     const uint32_t M = act_mask(x, a.next - 1u, v);
     const uint32_t* ru = x->lab + (size_t)v * 32u;
     uint32_t* rd = x->lab + (size_t)dst * 32u;
@@ -112,8 +114,24 @@ struct MsSsspOp {
 
 // ---- group kernels
 
+// checked build: the group's pointers read from device memory must be set and aligned
+__device__ __forceinline__ bool aux_ok(const TravCtx& c, const BatchAux* x) {
+#ifdef ALB_CHECKED
+  const uint64_t a = (uint64_t)x;
+  if (!ALB_IN_RANGE(c.chk, CHK_PTR, (a == 0 || (a & 7)) ? 1u : 0u, 1u)) return false;
+  const uint64_t l = (uint64_t)x->lab, s = (uint64_t)x->seen, p0 = (uint64_t)x->act0, p1 = (uint64_t)x->act1;
+  const bool bad = !l || (l & 3) || !s || (s & 3) || !p0 || (p0 & 7) || !p1 || (p1 & 7);
+  return ALB_IN_RANGE(c.chk, CHK_PTR, bad ? 2u : 0u, 1u);
+#else
+  (void)c;
+  (void)x;
+  return true;
+#endif
+}
+
 __global__ void __launch_bounds__(kBlock) k_batch_init(TravCtx c) {
   const BatchAux* x = static_cast<const BatchAux*>(c.args->aux);
+  if (!aux_ok(c, x)) return;
   const uint64_t n = c.n;
   for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < n * 32u;
        i += (uint64_t)gridDim.x * kBlock)
@@ -128,12 +146,20 @@ __global__ void __launch_bounds__(kBlock) k_batch_init(TravCtx c) {
 __global__ void k_batch_seed(TravCtx c) {
   const CallArgs* ca = c.args;
   const BatchAux* x = static_cast<const BatchAux*>(ca->aux);
+  if (!aux_ok(c, x)) return;
   const uint32_t s = threadIdx.x;
   if (s < ca->nsrc) {
     const uint32_t v = ca->srcs[s], bit = 1u << s;
+    if (v >= c.n) {  // only possible for sources passed in device memory
+      atomicOr(&c.st->status, ST_ERR_SRC);
+      return;
+    }
     x->lab[(size_t)v * 32u + s] = 0u;
     atomicOr(x->seen + v, bit);
-    if (act_or(x->act0 + v, 0u, bit)) c.F0[atomicAdd(&c.st->fcount[0], 1u)] = v;
+    if (act_or(x->act0 + v, 0u, bit)) {
+      const uint32_t slot = atomicAdd(&c.st->fcount[0], 1u);
+      if (ALB_IN_RANGE(c.chk, CHK_PUSH, slot, c.n)) c.F0[slot] = v;
+    }
   }
 }
 
@@ -142,6 +168,7 @@ __global__ void __launch_bounds__(kBlock) k_batch_out(TravCtx c) {
   __shared__ uint32_t tile[32][33];
   const CallArgs* ca = c.args;
   const BatchAux* x = static_cast<const BatchAux*>(ca->aux);
+  if (!aux_ok(c, x)) return;
   const uint32_t n = c.n, ns = ca->nsrc;
   uint32_t* out = ca->lab;
   const uint32_t tx = threadIdx.x & 31u, ty = threadIdx.x >> 5;  // 32 x 8
@@ -174,7 +201,14 @@ __global__ void k_multi_seed(TravCtx c) {
   const CallArgs* ca = c.args;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ca->nsrc; i += gridDim.x * blockDim.x) {
     const uint32_t v = ca->srcs[i];
-    if (atomicCAS(ca->lab + v, kInf, 0u) == kInf) c.F0[atomicAdd(&c.st->fcount[0], 1u)] = v;
+    if (v >= c.n) {  // only possible for sources passed in device memory
+      atomicOr(&c.st->status, ST_ERR_SRC);
+      continue;
+    }
+    if (atomicCAS(ca->lab + v, kInf, 0u) == kInf) {
+      const uint32_t slot = atomicAdd(&c.st->fcount[0], 1u);
+      if (ALB_IN_RANGE(c.chk, CHK_PUSH, slot, c.n)) c.F0[slot] = v;
+    }
   }
 }
 
@@ -209,7 +243,7 @@ alb_status free_batch(alb_graph g) {
   cudaFree(b->seen);
   cudaFree(b->act);
   cudaFree(b->aux);
-  cudaFree(b->srcs);
+  cudaFree(b->srcs);  // callers synchronise the device before freeing a workspace
   cudaFree(b->tmp);
   cudaGetLastError();
   delete b;
@@ -219,7 +253,9 @@ alb_status free_batch(alb_graph g) {
 
 alb_status batch_stats(alb_graph, alb_stats*) { return ALB_OK; }
 
-static alb_status ensure_batch(alb_graph g, bool group_arrays, uint32_t nsrc) {
+static __global__ void k_set_aux(BatchAux* dst, BatchAux v) { *dst = v; }
+
+static alb_status ensure_batch(alb_graph g, bool group_arrays, uint32_t nsrc, cudaStream_t s) {
   if (!g->batch) g->batch = new (std::nothrow) BatchWs();
   BatchWs* b = g->batch;
   if (!b) return ALB_ERR_OOM;
@@ -229,14 +265,19 @@ static alb_status ensure_batch(alb_graph g, bool group_arrays, uint32_t nsrc) {
     ALB_CUDA_TRY(cudaMalloc((void**)&b->seen, sizeof(uint32_t) * n));
     ALB_CUDA_TRY(cudaMalloc((void**)&b->act, sizeof(unsigned long long) * n * 2u));
     ALB_CUDA_TRY(cudaMalloc((void**)&b->aux, sizeof(BatchAux)));
+    // written on the call's stream: the batch kernels queued after it read it
     BatchAux h{b->lab, b->seen, b->act, b->act + n};
-    ALB_CUDA_TRY(cudaMemcpy(b->aux, &h, sizeof(h), cudaMemcpyHostToDevice));
+    k_set_aux<<<1, 1, 0, s>>>(b->aux, h);
+    ALB_CUDA_TRY(cudaGetLastError());
   }
   if (b->cap_srcs < nsrc) {
-    cudaFree(b->srcs);
+    // Stream-ordered: work already queued on s (an earlier batch's seed kernel) may still read
+    // the old buffer, and a plain cudaFree need not wait for it.
+    const uint32_t cap = nsrc < 1024u ? 1024u : nsrc;
+    if (b->srcs) ALB_CUDA_TRY(cudaFreeAsync(b->srcs, s));
     b->srcs = nullptr;
-    ALB_CUDA_TRY(cudaMalloc((void**)&b->srcs, sizeof(uint32_t) * nsrc));
-    b->cap_srcs = nsrc;
+    ALB_CUDA_TRY(cudaMallocAsync((void**)&b->srcs, sizeof(uint32_t) * cap, s));
+    b->cap_srcs = cap;
   }
   return ALB_OK;
 }
@@ -327,24 +368,22 @@ static alb_status build_batch_graph(alb_graph g, BatchKind kind) {
   return ALB_OK;
 }
 
+// Sources onto the device, stream-ordered and without a host round trip: host-memory sources are
+// checked here; device-memory sources are checked by the seed kernels (a bad one is skipped and
+// latched as ALB_ERR_INVALID_ARG, returned by alb_sync).
 static alb_status stage_srcs(alb_graph g, const uint32_t* hd_srcs, uint32_t k, cudaStream_t s) {
   BatchWs* b = g->batch;
+  if (!is_device_ptr(hd_srcs)) {
+    for (uint32_t i = 0; i < k; ++i)
+      if (hd_srcs[i] >= g->n) return ALB_ERR_INVALID_ARG;
+  }
   ALB_CUDA_TRY(cudaMemcpyAsync(b->srcs, hd_srcs, sizeof(uint32_t) * k, cudaMemcpyDefault, s));
-  // every source must be a vertex: checked on the host copy
-  uint32_t* h = (uint32_t*)std::malloc(sizeof(uint32_t) * (k ? k : 1));
-  if (!h) return ALB_ERR_OOM;
-  cudaError_t e = cudaMemcpyAsync(h, b->srcs, sizeof(uint32_t) * k, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  bool ok = e == cudaSuccess;
-  for (uint32_t i = 0; ok && i < k; ++i) ok = h[i] < g->n;
-  std::free(h);
-  if (e != cudaSuccess) return ALB_ERR_CUDA;
-  return ok ? ALB_OK : ALB_ERR_INVALID_ARG;
+  return ALB_OK;
 }
 
 static alb_status run_groups(alb_graph g, BatchKind kind, const uint32_t* hd_srcs, uint32_t k,
                              uint32_t* out, cudaStream_t s) {
-  alb_status rc = ensure_batch(g, true, k);
+  alb_status rc = ensure_batch(g, true, k, s);
   if (rc != ALB_OK) return rc;
   BatchWs* b = g->batch;
   if ((rc = stage_srcs(g, hd_srcs, k, s)) != ALB_OK) return rc;
@@ -370,7 +409,7 @@ static alb_status run_groups(alb_graph g, BatchKind kind, const uint32_t* hd_src
 
 static alb_status run_multi(alb_graph g, BatchKind kind, const uint32_t* hd_srcs, uint32_t k,
                             uint32_t* out, cudaStream_t s) {
-  alb_status rc = ensure_batch(g, false, k);
+  alb_status rc = ensure_batch(g, false, k, s);
   if (rc != ALB_OK) return rc;
   BatchWs* b = g->batch;
   if ((rc = stage_srcs(g, hd_srcs, k, s)) != ALB_OK) return rc;

@@ -8,10 +8,30 @@ namespace alb {
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
+// Bounds checks of the checked build: an index outside [0, bound) records (code, index,
+// bound) once in chk and counts every failure in chk[3]; the caller skips the access.
+#ifdef ALB_CHECKED
+__device__ __forceinline__ bool in_range(uint32_t* chk, uint32_t code, uint64_t idx, uint64_t bound) {
+  if (idx < bound) return true;
+  if (chk) {
+    if (atomicCAS(chk, 0u, code) == 0u) {
+      chk[1] = (uint32_t)idx;
+      chk[2] = (uint32_t)bound;
+    }
+    atomicAdd(chk + 3, 1u);
+  }
+  return false;
+}
+#define ALB_IN_RANGE(chk, code, idx, bound) ::alb::in_range((chk), (code), (uint64_t)(idx), (uint64_t)(bound))
+#else
+#define ALB_IN_RANGE(chk, code, idx, bound) true
+#endif
+
 // Warp-aggregated append of `v` for every lane with `pred`: one atomicAdd on
 // `count` per warp (ballot + popc), lanes write consecutive slots. Every lane of
 // the warp must call it (the callers keep their loops warp-uniform).
-__device__ __forceinline__ void warp_append(bool pred, uint32_t v, uint32_t* buf, uint32_t* count) {
+__device__ __forceinline__ void warp_append(bool pred, uint32_t v, uint32_t* buf, uint32_t* count,
+                                            uint32_t cap = 0xFFFFFFFFu, uint32_t* chk = nullptr) {
   const unsigned mask = __ballot_sync(kFull, pred);
   if (mask == 0) return;
   const uint32_t lane = lane_id();
@@ -19,7 +39,10 @@ __device__ __forceinline__ void warp_append(bool pred, uint32_t v, uint32_t* buf
   uint32_t base = 0;
   if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(mask));
   base = __shfl_sync(kFull, base, leader);
-  if (pred) buf[base + __popc(mask & ((1u << lane) - 1u))] = v;
+  const uint32_t slot = base + __popc(mask & ((1u << lane) - 1u));
+  if (pred && ALB_IN_RANGE(chk, 4u, slot, cap)) buf[slot] = v;
+  (void)cap;
+  (void)chk;
 }
 
 // Inclusive warp scan (Kogge-Stone over shuffles).

@@ -66,9 +66,13 @@ __global__ void k_scan_graph(const uint32_t* off, const uint32_t* idx, const uin
 }
 
 static void free_graph_memory(alb_graph g) {
-  cudaFree(g->off);
-  cudaFree(g->idx);
-  cudaFree(g->w);
+  if (!g->csr_refs || --(*g->csr_refs) == 0) {
+    cudaFree(g->off);
+    cudaFree(g->idx);
+    cudaFree(g->w);
+    delete g->csr_refs;
+  }
+  g->csr_refs = nullptr;
   cudaFree(g->F0);
   cudaFree(g->F1);
   cudaFree(g->hub_v);
@@ -77,11 +81,34 @@ static void free_graph_memory(alb_graph g) {
   cudaFree(g->tmp);
   cudaFree(g->st);
   cudaFree(g->args);
+  cudaFree(g->chk);
   if (g->h_st) cudaFreeHost(g->h_st);
   cudaGetLastError();
 }
 
 // Launch configuration of application `app` for parameters p.
+// Per-handle round workspace (two frontiers, huge worklist + prefix, stamps, state).
+static alb_status alloc_workspace(alb_graph g) {
+  const size_t nb = sizeof(uint32_t) * (size_t)g->n;
+  cudaError_t e = cudaMalloc((void**)&g->F0, nb);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&g->F1, nb);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&g->hub_v, nb + sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&g->hub_p, nb + sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&g->stamp, nb);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&g->st, sizeof(RoundState));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&g->args, sizeof(CallArgs));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&g->h_st, sizeof(RoundState));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&g->chk, 4 * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(g->chk, 0, 4 * sizeof(uint32_t));
+  // the memset runs on the legacy stream, which callers' non-blocking streams do not wait for
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? ALB_ERR_OOM : ALB_ERR_CUDA;
+  }
+  return ALB_OK;
+}
+
 static void apply_launch_config(alb_graph g, int app, const alb_params& p) {
   uint32_t occ_i = 1, occ_l = 1;
   occupancy(&occ_i, &occ_l);
@@ -106,7 +133,8 @@ void select_cfg(alb_graph g, int app) {
 }
 
 alb_status latch_from_state(alb_graph g, uint32_t status) {
-  if (status & ST_ERR_INDEX) g->latched = ALB_ERR_DEVICE;
+  if (status & ST_ERR_SRC) g->latched = ALB_ERR_INVALID_ARG;
+  else if (status & ST_ERR_INDEX) g->latched = ALB_ERR_DEVICE;
   else if (status & ST_ERR_ROUNDS) g->latched = ALB_ERR_TIMEOUT;
   return g->latched;
 }
@@ -118,6 +146,22 @@ using namespace alb;
 extern "C" {
 
 uint32_t alb_version(void) { return 10000u; }
+
+uint32_t alb_checked_build(void) {
+#ifdef ALB_CHECKED
+  return 1u;
+#else
+  return 0u;
+#endif
+}
+
+alb_status alb_debug_check(alb_graph g, uint32_t* out4) {
+  if (!g || !out4) return ALB_ERR_INVALID_ARG;
+  if (cudaSetDevice(g->device) != cudaSuccess) return ALB_ERR_CUDA;
+  ALB_CUDA_TRY(cudaStreamSynchronize(g->last_stream));
+  ALB_CUDA_TRY(cudaMemcpy(out4, g->chk, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  return ALB_OK;
+}
 
 const char* alb_status_str(alb_status s) {
   switch (s) {
@@ -189,22 +233,18 @@ alb_status alb_graph_create(uint32_t n, uint64_t m, const uint32_t* hd_offsets,
   g->has_w = hd_weights != nullptr || m == 0;  // a graph without edges has nothing to weigh
   const size_t nb = sizeof(uint32_t) * (size_t)n;
   const size_t mb = sizeof(uint32_t) * (size_t)(m ? m : 1);
+  g->csr_refs = new (std::nothrow) int(1);
+  if (!g->csr_refs) return fail(ALB_ERR_OOM);
   cudaError_t e = cudaSuccess;
   e = cudaMalloc((void**)&g->off, nb + sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc((void**)&g->idx, mb);
   if (e == cudaSuccess && g->has_w) e = cudaMalloc((void**)&g->w, mb);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&g->F0, nb);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&g->F1, nb);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&g->hub_v, nb + sizeof(uint32_t));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&g->hub_p, nb + sizeof(uint32_t));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&g->stamp, nb);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&g->st, sizeof(RoundState));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&g->args, sizeof(CallArgs));
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&g->h_st, sizeof(RoundState));
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(e == cudaErrorMemoryAllocation ? ALB_ERR_OOM : ALB_ERR_CUDA);
   }
+  alb_status wrc = alloc_workspace(g);
+  if (wrc != ALB_OK) return fail(wrc);
   e = cudaMemcpyAsync(g->off, hd_offsets, nb + sizeof(uint32_t), cudaMemcpyDefault, s);
   if (e == cudaSuccess && m) e = cudaMemcpyAsync(g->idx, hd_indices, sizeof(uint32_t) * m, cudaMemcpyDefault, s);
   if (e == cudaSuccess && hd_weights && m)
@@ -238,10 +278,42 @@ alb_status alb_graph_create(uint32_t n, uint64_t m, const uint32_t* hd_offsets,
   return ALB_OK;
 }
 
+alb_status alb_graph_clone(alb_graph src, alb_graph* out) {
+  if (!src || !out) return ALB_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (cudaSetDevice(src->device) != cudaSuccess) return ALB_ERR_CUDA;
+  alb_graph g = new (std::nothrow) alb_graph_s();
+  if (!g) return ALB_ERR_OOM;
+  g->device = src->device;
+  g->n = src->n;
+  g->m = src->m;
+  g->flags = src->flags;
+  g->has_w = src->has_w;
+  g->max_w = src->max_w;
+  g->max_deg = src->max_deg;
+  g->off = src->off;
+  g->idx = src->idx;
+  g->w = src->w;
+  g->csr_refs = src->csr_refs;
+  ++(*g->csr_refs);
+  g->num_sms = src->num_sms;
+  for (int a = 0; a < 5; ++a) g->cfg[a] = src->cfg[a];
+  select_cfg(g, ALB_APP_BFS);
+  alb_status rc = alloc_workspace(g);
+  if (rc != ALB_OK) {
+    free_graph_memory(g);
+    delete g;
+    return rc;
+  }
+  *out = g;
+  return ALB_OK;
+}
+
 alb_status alb_graph_destroy(alb_graph g) {
   if (!g) return ALB_ERR_INVALID_ARG;
   cudaSetDevice(g->device);
-  cudaStreamSynchronize(g->last_stream);
+  // the handle may have queued work on several streams; none may still use what is freed
+  cudaDeviceSynchronize();
   free_traversal_graphs(g);
   free_pagerank(g);
   free_batch(g);
@@ -253,7 +325,7 @@ alb_status alb_graph_destroy(alb_graph g) {
 alb_status alb_set_params(alb_graph g, const alb_params* p) {
   if (!g || !p || !params_valid(p)) return ALB_ERR_INVALID_ARG;
   cudaSetDevice(g->device);
-  cudaStreamSynchronize(g->last_stream);
+  cudaDeviceSynchronize();  // cached graphs and workspaces are freed below
   free_traversal_graphs(g);
   free_pagerank(g);
   free_batch(g);
@@ -271,7 +343,7 @@ alb_status alb_get_params(alb_graph g, alb_params* p) {
 alb_status alb_set_app_params(alb_graph g, alb_app app, const alb_params* p) {
   if (!g || !p || app < ALB_APP_BFS || app > ALB_APP_KCORE || !params_valid(p)) return ALB_ERR_INVALID_ARG;
   cudaSetDevice(g->device);
-  cudaStreamSynchronize(g->last_stream);
+  cudaDeviceSynchronize();  // cached graphs and workspaces are freed below
   // only the cached work of this application depends on its parameters
   switch (app) {
     case ALB_APP_PAGERANK: free_pagerank(g); break;

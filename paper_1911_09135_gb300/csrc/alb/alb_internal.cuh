@@ -19,7 +19,7 @@ constexpr int kHubSmem = 2048;          // huge vertices the LB kernel stages in
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 
 // Latched device error bits.
-enum : uint32_t { ST_ERR_ROUNDS = 1u, ST_ERR_INDEX = 2u };
+enum : uint32_t { ST_ERR_ROUNDS = 1u, ST_ERR_INDEX = 2u, ST_ERR_SRC = 4u };
 
 enum App : int { APP_BFS = 0, APP_SSSP = 1, APP_CC = 2, APP_KCORE = 3, APP_TRACE = 4, APP_COUNT = 5 };
 
@@ -66,7 +66,7 @@ struct TravCtx {
   uint32_t distribution;  // 0 cyclic, 1 blocked (Algorithm 2)
   uint32_t max_rounds;
   uint32_t use_graph;     // conditional handles valid
-  uint32_t pad;
+  uint32_t m;             // CSR entries (bounds of the checked build)
   uint32_t* F0;           // frontier buffers (round parity 0 / 1)
   uint32_t* F1;
   uint32_t* hub_v;        // huge worklist "work"
@@ -76,6 +76,21 @@ struct TravCtx {
   const CallArgs* args;
   cudaGraphConditionalHandle h_while;
   cudaGraphConditionalHandle h_if;
+  uint32_t* chk;          // checked build: first failed bound (code, index, bound, count)
+};
+
+// Codes recorded by the checked build (-DALB_CHECKED) when an index is out of range; the
+// access is skipped instead of faulting.
+enum : uint32_t {
+  CHK_EDGE = 1,      // edge index >= m
+  CHK_DST = 2,       // destination vertex >= n
+  CHK_FRONTIER = 3,  // frontier entry >= n
+  CHK_PUSH = 4,      // next-frontier slot >= n
+  CHK_HUB = 5,       // huge-worklist slot > n
+  CHK_ROW = 6,       // multi-source label row >= n
+  CHK_SRC = 7,       // LB source index >= number of huge vertices
+  CHK_STATE = 8,     // round state out of range (frontier size > n, huge count > n, edges > m)
+  CHK_PTR = 9,       // a pointer read from device memory is null or misaligned
 };
 
 }  // namespace alb
@@ -92,6 +107,7 @@ struct alb_graph_s {
   uint32_t* off = nullptr;
   uint32_t* idx = nullptr;
   uint32_t* w = nullptr;
+  int* csr_refs = nullptr;  // handles sharing off/idx/w (alb_graph_clone); the last one frees them
 
   // per-application launch configuration (indexed by alb_app); the fields below hold the
   // configuration of the application being called (select_cfg copies it in)
@@ -115,6 +131,7 @@ struct alb_graph_s {
   alb::RoundState* st = nullptr;
   alb::CallArgs* args = nullptr;
   alb::RoundState* h_st = nullptr;  // pinned mirror
+  uint32_t* chk = nullptr;          // 4 words: checked-build bound failures (never reset)
 
   cudaGraph_t graph[alb::APP_COUNT] = {};
   cudaGraphExec_t exec[alb::APP_COUNT] = {};

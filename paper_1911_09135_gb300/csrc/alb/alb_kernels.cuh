@@ -31,6 +31,8 @@ struct OpArgs {
   uint32_t next;  // round + 1
   uint32_t k;
   const void* aux;  // operator-specific state (the multi-source operators)
+  uint32_t n;
+  uint32_t* chk;    // checked build
 };
 
 // bfs (push): level[dst] = round + 1 if unvisited.
@@ -102,11 +104,16 @@ struct aggregates<Op, decltype(void(Op::kAggregate))> { static constexpr bool va
 // thread keeps U independent memory requests in flight. Warp-uniform callers.
 template <class Op, int U>
 __device__ __forceinline__ void relax(const TravCtx& c, const OpArgs& a, const uint32_t (&e)[U],
-                                      const bool (&ok)[U], const uint32_t (&sv)[U], uint32_t* Fn,
+                                      const bool (&ok_in)[U], const uint32_t (&sv)[U], uint32_t* Fn,
                                       uint32_t* ncount) {
   uint32_t dst[U], wt[U];
+  bool ok[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) ok[u] = ok_in[u] && ALB_IN_RANGE(c.chk, CHK_EDGE, e[u], c.m);
 #pragma unroll
   for (int u = 0; u < U; ++u) dst[u] = ok[u] ? __ldcs(c.idx + e[u]) : 0u;  // streamed once: evict-first
+#pragma unroll
+  for (int u = 0; u < U; ++u) ok[u] = ok[u] && ALB_IN_RANGE(c.chk, CHK_DST, dst[u], c.n);
 #pragma unroll
   for (int u = 0; u < U; ++u) wt[u] = (Op::kW && ok[u]) ? __ldcs(c.w + e[u]) : 0u;
   if constexpr (Op::kBatch) {
@@ -114,7 +121,7 @@ __device__ __forceinline__ void relax(const TravCtx& c, const OpArgs& a, const u
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const bool push = ok[u] && Op::apply(a, sv[u], dst[u], wt[u]);
-      warp_append(push, dst[u], Fn, ncount);
+      warp_append(push, dst[u], Fn, ncount, c.n, c.chk);
     }
   } else if constexpr (aggregates<Op>::value) {
     uint32_t cur[U];
@@ -130,7 +137,7 @@ __device__ __forceinline__ void relax(const TravCtx& c, const OpArgs& a, const u
         const unsigned grp = __match_any_sync(wm, dst[u]);
         if ((int)lane == __ffs(grp) - 1) push = Op::commit_n(a, dst[u], (uint32_t)__popc(grp));
       }
-      warp_append(push, dst[u], Fn, ncount);
+      warp_append(push, dst[u], Fn, ncount, c.n, c.chk);
     }
   } else {
     uint32_t cur[U];
@@ -139,7 +146,7 @@ __device__ __forceinline__ void relax(const TravCtx& c, const OpArgs& a, const u
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const bool push = ok[u] && Op::want(a, sv[u], cur[u], wt[u]) && Op::commit(a, sv[u], dst[u], wt[u]);
-      warp_append(push, dst[u], Fn, ncount);
+      warp_append(push, dst[u], Fn, ncount, c.n, c.chk);
     }
   }
 }
@@ -178,7 +185,8 @@ static __device__ void finish_round(const TravCtx& c) {
 // Append huge vertices to `work` with their prefixWork entry: one 64-bit atomic
 // per warp adds (count << 32 | degree sum), so slot order and prefix order agree.
 static __device__ __forceinline__ void hub_append(bool huge, uint32_t v, uint32_t deg, uint32_t* hub_v,
-                                           uint32_t* hub_p, unsigned long long* packed) {
+                                           uint32_t* hub_p, unsigned long long* packed,
+                                           uint32_t cap = 0xFFFFFFFFu, uint32_t* chk = nullptr) {
   const unsigned mask = __ballot_sync(kFull, huge);
   if (mask == 0) return;
   const uint32_t lane = lane_id();
@@ -191,9 +199,13 @@ static __device__ __forceinline__ void hub_append(bool huge, uint32_t v, uint32_
   old = __shfl_sync(kFull, old, leader);
   if (huge) {
     const uint32_t slot = (uint32_t)(old >> 32) + __popc(mask & ((1u << lane) - 1u));
-    hub_v[slot] = v;
-    hub_p[slot] = (uint32_t)old + (incl - x);
+    if (ALB_IN_RANGE(chk, CHK_HUB, slot, cap)) {
+      hub_v[slot] = v;
+      hub_p[slot] = (uint32_t)old + (incl - x);
+    }
   }
+  (void)cap;
+  (void)chk;
 }
 
 // ----------------------------------------------------- inspection + TWC kernel
@@ -210,12 +222,13 @@ __global__ void __launch_bounds__(kBlock) k_inspect(TravCtx c) {
   const uint32_t r = st->round;
   const uint32_t cur = r & 1u;
   const bool all = st->all_active != 0u;
-  const uint32_t nf = all ? c.n : st->fcount[cur];
+  uint32_t nf = all ? c.n : st->fcount[cur];
+  if (!ALB_IN_RANGE(c.chk, CHK_STATE, nf, (uint64_t)c.n + 1u)) nf = 0u;
   const uint32_t* F = cur ? c.F1 : c.F0;
   uint32_t* Fn = cur ? c.F0 : c.F1;
   uint32_t* ncount = &st->fcount[cur ^ 1u];
   const CallArgs* ca = c.args;
-  const OpArgs a{ca->lab, c.stamp, r + 1u, ca->k, ca->aux};
+  const OpArgs a{ca->lab, c.stamp, r + 1u, ca->k, ca->aux, c.n, c.chk};
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   unsigned long long twc_edges = 0ull;
 
@@ -229,10 +242,11 @@ __global__ void __launch_bounds__(kBlock) k_inspect(TravCtx c) {
     const uint64_t base = (uint64_t)s_tile * kBlock;
     if (base >= nf) break;  // CTA-uniform
     const uint32_t i = (uint32_t)base + tid;
-    const bool valid = i < nf;
+    bool valid = i < nf;
     uint32_t v = 0u, beg = 0u, deg = 0u, sv = 0u;
+    if (valid) v = all ? i : F[i];
+    if (valid && !ALB_IN_RANGE(c.chk, CHK_FRONTIER, v, c.n)) valid = false;
     if (valid) {
-      v = all ? i : F[i];
       beg = c.off[v];
       deg = c.off[v + 1] - beg;
       sv = Op::sval(a, v);
@@ -242,7 +256,7 @@ __global__ void __launch_bounds__(kBlock) k_inspect(TravCtx c) {
     const bool wrp = valid && !huge && !cta && deg >= c.warp_min;
     const uint32_t sdeg = (valid && !huge && !cta && !wrp) ? deg : 0u;
     if (valid && !huge) twc_edges += deg;
-    hub_append(huge, v, deg, c.hub_v, c.hub_p, &st->hub_packed);
+    hub_append(huge, v, deg, c.hub_v, c.hub_p, &st->hub_packed, c.n + 1u, c.chk);
     if (cta) {
       const uint32_t s = atomicAdd(&s_ncta, 1u);
       s_cb[s] = beg; s_cd[s] = deg; s_cv[s] = sv;
@@ -339,20 +353,27 @@ __global__ void __launch_bounds__(kBlock) k_lb(TravCtx c) {
 
   RoundState* st = c.st;
   const unsigned long long hp = st->hub_packed;
-  const uint32_t nh = (uint32_t)(hp >> 32);
-  const uint32_t e = (uint32_t)hp;
+  uint32_t nh = (uint32_t)(hp >> 32);
+  uint32_t e = (uint32_t)hp;
+  if (!ALB_IN_RANGE(c.chk, CHK_STATE, nh, (uint64_t)c.n + 1u) ||
+      !ALB_IN_RANGE(c.chk, CHK_STATE, e, (uint64_t)c.m + 1u)) {
+    nh = 0u;
+    e = 0u;
+  }
   const uint32_t r = st->round;
   const uint32_t cur = r & 1u;
   uint32_t* Fn = cur ? c.F0 : c.F1;
   uint32_t* ncount = &st->fcount[cur ^ 1u];
   const CallArgs* ca = c.args;
-  const OpArgs a{ca->lab, c.stamp, r + 1u, ca->k, ca->aux};
+  const OpArgs a{ca->lab, c.stamp, r + 1u, ca->k, ca->aux, c.n, c.chk};
   const uint32_t tid = threadIdx.x, lane = tid & 31u;
 
   const bool staged = nh <= (uint32_t)kStage;
   if (staged) {
     for (uint32_t j = tid; j < nh; j += kBlock) {
-      const uint32_t u = c.hub_v[j], p = c.hub_p[j];
+      uint32_t u = c.hub_v[j];
+      const uint32_t p = c.hub_p[j];
+      if (!ALB_IN_RANGE(c.chk, CHK_FRONTIER, u, c.n)) u = 0u;
       s_p[j] = p;
       s_base[j] = c.off[u] - p;
       if constexpr (kTrace) s_src[j] = u;
@@ -366,13 +387,15 @@ __global__ void __launch_bounds__(kBlock) k_lb(TravCtx c) {
   uint32_t j = 0u, jc = kInf, base_c = 0u, val_c = 0u, src_c = 0u;
   auto resolve = [&](uint32_t k, uint32_t& edge, uint32_t& sv, uint32_t& src) {
     j = upper_search(P, j, nh, k);
+    if (!ALB_IN_RANGE(c.chk, CHK_SRC, j, nh)) j = 0u;
     if (staged) {
       edge = k + s_base[j];
       if constexpr (kTrace) { src = s_src[j]; sv = 0u; }
       else { sv = s_val[j]; src = 0u; }
     } else {
       if (j != jc) {
-        const uint32_t u = c.hub_v[j];
+        uint32_t u = c.hub_v[j];
+        if (!ALB_IN_RANGE(c.chk, CHK_FRONTIER, u, c.n)) u = 0u;
         base_c = c.off[u] - c.hub_p[j];
         if constexpr (!kTrace) val_c = Op::sval(a, u);
         src_c = u;
@@ -454,7 +477,7 @@ __global__ void __launch_bounds__(kBlock) k_init(TravCtx c) {
     } else if constexpr (APP == APP_KCORE) {
       uint32_t d = 0u;
       if (ok) { d = c.off[v + 1] - c.off[v]; lab[v] = d; }
-      warp_append(ok && d < k, v, c.F0, &st->fcount[0]);
+      warp_append(ok && d < k, v, c.F0, &st->fcount[0], c.n, c.chk);
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {

@@ -574,7 +574,8 @@ static alb_status pr_setup(alb_graph g, cudaStream_t s) {
   // runs of <= kFinDirect slots are summed directly by the hub's warp
   {
     std::vector<uint32_t> hp((size_t)w->nh + 1);
-    ALB_CUDA_TRY(cudaMemcpy(hp.data(), w->hub_p, sizeof(uint32_t) * hp.size(), cudaMemcpyDeviceToHost));
+    ALB_CUDA_TRY(cudaMemcpyAsync(hp.data(), w->hub_p, sizeof(uint32_t) * hp.size(), cudaMemcpyDeviceToHost, s));
+    ALB_CUDA_TRY(cudaStreamSynchronize(s));
     std::vector<uint32_t> ts, tl, t0((size_t)w->nh + 1, 0u);
     for (uint32_t j = 0; j < w->nh; ++j) {
       t0[j] = (uint32_t)ts.size();
@@ -589,15 +590,18 @@ static alb_status pr_setup(alb_graph g, cudaStream_t s) {
     t0[w->nh] = (uint32_t)ts.size();
     w->ntask = (uint32_t)ts.size();
     ALB_CUDA_TRY(cudaMalloc((void**)&w->hub_t0, sizeof(uint32_t) * t0.size()));
-    ALB_CUDA_TRY(cudaMemcpy(w->hub_t0, t0.data(), sizeof(uint32_t) * t0.size(), cudaMemcpyHostToDevice));
+    // stream-ordered with the kernels that read them (the caller's stream may not block on the
+    // legacy default stream), and complete before the host vectors go out of scope
+    ALB_CUDA_TRY(cudaMemcpyAsync(w->hub_t0, t0.data(), sizeof(uint32_t) * t0.size(), cudaMemcpyHostToDevice, s));
     const size_t nt = ts.size() ? ts.size() : 1;
     ALB_CUDA_TRY(cudaMalloc((void**)&w->task_start, sizeof(uint32_t) * nt));
     ALB_CUDA_TRY(cudaMalloc((void**)&w->task_len, sizeof(uint32_t) * nt));
     ALB_CUDA_TRY(cudaMalloc((void**)&w->part2, sizeof(float) * nt));
     if (!ts.empty()) {
-      ALB_CUDA_TRY(cudaMemcpy(w->task_start, ts.data(), sizeof(uint32_t) * ts.size(), cudaMemcpyHostToDevice));
-      ALB_CUDA_TRY(cudaMemcpy(w->task_len, tl.data(), sizeof(uint32_t) * tl.size(), cudaMemcpyHostToDevice));
+      ALB_CUDA_TRY(cudaMemcpyAsync(w->task_start, ts.data(), sizeof(uint32_t) * ts.size(), cudaMemcpyHostToDevice, s));
+      ALB_CUDA_TRY(cudaMemcpyAsync(w->task_len, tl.data(), sizeof(uint32_t) * tl.size(), cudaMemcpyHostToDevice, s));
     }
+    ALB_CUDA_TRY(cudaStreamSynchronize(s));
   }
   ALB_CUDA_TRY(cudaGetLastError());
   w->ready = true;

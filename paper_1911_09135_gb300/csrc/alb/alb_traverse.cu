@@ -118,6 +118,8 @@ TravCtx make_ctx(alb_graph g, bool use_graph, cudaGraphConditionalHandle hw,
   c.args = g->args;
   c.h_while = hw;
   c.h_if = hi;
+  c.m = (uint32_t)g->m;
+  c.chk = g->chk;
   return c;
 }
 

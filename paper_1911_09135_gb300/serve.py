@@ -1,12 +1,17 @@
 """Continuous-batching query server over resident graphs (bfs / sssp / cc).
 
-Graphs are uploaded once and stay resident, each with its own CUDA stream (a slot). Requests
-arrive open-loop; each is queued on its graph. Whenever a graph's slot is idle and queued work
-exists, the server forms one batch from that graph's queue - up to 32 bfs sources and 32 sssp
+Graphs are uploaded once and stay resident. Each has one or more slots (a handle with its own
+CUDA stream; extra slots are clones sharing the graph's device CSR, given to large graphs).
+Smaller graphs run on higher-priority streams, and every slot's grid is sized to its graph
+(at most two CTAs per SM), so kernels of several slots share the SMs. Requests arrive open-loop; each is queued
+on its graph. Whenever one of a graph's slots is idle
+and queued work exists, the server forms one batch from that graph's queue - up to 32 bfs sources and 32 sssp
 sources (one multi-source group each, sharing every CSR read: alb_bfs_batch / alb_sssp_batch)
-plus every queued cc query (one alb_cc serves them all) - admits it only if free device memory
-covers its output buffers, launches it on the slot's stream and copies the requested rows to
-pinned host memory. Slots of different graphs run concurrently on the device, and requests that
+plus every queued cc query (one alb_cc serves them all), launches it on the slot's stream and
+copies the requested rows to pinned host memory. Device memory is admitted per slot: a slot
+(its result buffers and workspaces) is created only if free HBM covers it, and no batch is
+launched while free HBM is below a reserve (memory taken by other users of the GPU); the
+slots' buffers are allocated up front, so nothing is allocated while kernels run. Slots of different graphs run concurrently on the device, and requests that
 arrive meanwhile wait for the next batch of their graph. A request's latency runs from its
 arrival to the completion of its result's device-to-host copy.
 
@@ -15,6 +20,7 @@ All traversal work runs in libalb.so; this module only schedules calls.
 from __future__ import annotations
 
 import dataclasses
+import os
 import time
 from collections import deque
 
@@ -24,6 +30,7 @@ from . import alb
 
 GROUP = 32
 KINDS = ("bfs", "sssp", "cc")
+EDGES_PER_CTA = 1 << 17       # serving grids: one CTA per this many edges, at most 2 per SM
 
 
 @dataclasses.dataclass
@@ -54,100 +61,157 @@ def poisson_requests(graphs, count: int, rate: float, seed: int = 5) -> list[Req
 
 
 class _Slot:
-    def __init__(self, torch, csr, tune: bool):
-        self.torch = torch
+    """One handle (the graph's own, or a clone sharing its CSR) with its stream and buffers."""
+
+    def __init__(self, torch, G, n, priority: int):
+        self.G = G
+        self.n = n
+        self.stream = torch.cuda.Stream(priority=priority)
+        self.busy = None      # (event, batch info) while a batch is in flight
+        # Result buffers of one batch, allocated once: nothing is allocated while other slots'
+        # kernels run (an allocation can wait for the whole device).
+        self.d_bfs = torch.empty(GROUP * n, dtype=torch.int32, device="cuda")
+        self.d_sssp = torch.empty(GROUP * n, dtype=torch.int32, device="cuda")
+        self.d_cc = torch.empty(n, dtype=torch.int32, device="cuda")
+        self.h_bfs = torch.empty(GROUP * n, dtype=torch.int32).pin_memory()
+        self.h_sssp = torch.empty(GROUP * n, dtype=torch.int32).pin_memory()
+        self.h_cc = torch.empty(n, dtype=torch.int32).pin_memory()
+        self.h_srcs = torch.empty(2 * GROUP, dtype=torch.int32).pin_memory()
+
+    def warm(self, src: int):
+        """First use of every call on this slot (workspace allocation, graph instantiation)."""
+        self.h_srcs[0] = src
+        self.h_srcs[GROUP] = src
+        alb.alb_bfs_batch(self.G.h, self.h_srcs[:1], 1, self.d_bfs, self.stream)
+        alb.alb_sssp_batch(self.G.h, self.h_srcs[GROUP:GROUP + 1], 1, self.d_sssp, self.stream)
+        alb.alb_cc(self.G.h, self.d_cc, self.stream)
+        self.stream.synchronize()
+
+
+class _Graph:
+    """A resident graph: its request queues and one or more slots."""
+
+    @staticmethod
+    def slot_bytes(n: int) -> int:
+        """Device memory one slot holds: result buffers (2 x 32 labels + 1 per vertex), the
+        multi-source workspace (148 bytes per vertex) and the round workspace (20 per vertex)."""
+        return n * (4 * (2 * GROUP + 1) + 148 + 20)
+
+    def __init__(self, torch, csr, tune: bool, slots: int, priority: int):
         self.n = csr.n
         self.m = csr.m
         self.deg = csr.degrees().astype(np.int64)
         dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
-        self.G = alb.Graph(csr.n, dev(csr.offsets), dev(csr.indices), dev(csr.weights),
-                           symmetric=csr.symmetric)
-        self.stream = torch.cuda.Stream()
-        self.queue = {k: deque() for k in KINDS}
-        self.busy = None      # (event, batch info) while a batch is in flight
-        # pinned host staging for one batch's results
-        self.h_bfs = torch.empty(GROUP * csr.n, dtype=torch.int32).pin_memory()
-        self.h_sssp = torch.empty(GROUP * csr.n, dtype=torch.int32).pin_memory()
-        self.h_cc = torch.empty(csr.n, dtype=torch.int32).pin_memory()
+        G = alb.Graph(csr.n, dev(csr.offsets), dev(csr.indices), dev(csr.weights),
+                      symmetric=csr.symmetric)
+        # A persistent grid over the whole GPU would keep other slots' kernels waiting until it
+        # ends: small graphs get a grid sized to their edges, large ones two CTAs per SM, so
+        # kernels of several slots share the SMs.
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        G.set_params(grid_blocks=min(2 * sms, max(16, -(-csr.m // EDGES_PER_CTA))))
         if tune:
             src = int(np.argmax(self.deg))
             for k in KINDS:
-                self.G.autotune(k, src, reps=1)
+                G.autotune(k, src, reps=1)
+        handles = [G]
+        for _ in range(slots - 1):  # extra slots only while free device memory allows
+            free, _ = torch.cuda.mem_get_info()
+            if free < 2 * self.slot_bytes(csr.n) + (1 << 30):
+                break
+            handles.append(G.clone())  # clones keep the tuned knobs
+        self.slots = [_Slot(torch, h, csr.n, priority) for h in handles]
+        for sl in self.slots:
+            sl.warm(int(np.argmax(self.deg)))
+        self.queue = {k: deque() for k in KINDS}
+        self.log = []         # (seconds in flight, #bfs, #sssp, #cc) per completed batch
 
     def batch_bytes(self, nb, ns, nc) -> int:
-        return 4 * self.n * (nb + ns + (1 if nc else 0))
+        # result buffers are allocated with the slot; a batch needs no further device memory
+        return 0
 
     def close(self):
-        self.G.close()
+        for s in reversed(self.slots):
+            s.G.close()
 
 
 class Server:
     """One slot per resident graph; see the module docstring."""
 
     def __init__(self, graphs, *, tune: bool = True, keep_results: bool = False,
-                 hbm_reserve: int = 1 << 30):
+                 hbm_reserve: int = 1 << 30, big_graph_edges: int = 50_000_000, big_slots: int = 2):
         import torch
         self.torch = torch
-        self.slots = [_Slot(torch, g, tune) for g in graphs]
+        # smaller graphs get higher stream priority, so their short rounds are scheduled
+        # between the round kernels of large graphs instead of waiting behind them
+        lo, hi = torch.cuda.Stream.priority_range()
+        order = np.argsort(np.argsort([g.m for g in graphs]))
+        prio = [hi if order[i] < len(graphs) // 2 else lo for i in range(len(graphs))]
+        self.graphs = [_Graph(torch, g, tune, big_slots if g.m >= big_graph_edges else 1, prio[i])
+                       for i, g in enumerate(graphs)]
         self.keep = keep_results
         self.reserve = hbm_reserve
         self.results: dict[int, np.ndarray] = {}
         self.batches = 0
         self.deferred = 0     # batch formations postponed for lack of free device memory
         self.edges = 0        # traversed-edge units of completed requests (m of the graph each)
+        # with the bounds-checked library, every completed batch's record is inspected
+        self.checked = os.environ.get("ALB_CHECKED") == "1" and alb.alb_checked_build() == 1
 
     def close(self):
-        for s in self.slots:
-            s.close()
+        for g in self.graphs:
+            g.close()
 
     def _free_bytes(self) -> int:
         free, _ = self.torch.cuda.mem_get_info()
         cached = self.torch.cuda.memory_reserved() - self.torch.cuda.memory_allocated()
         return int(free + cached)
 
-    def _launch(self, s: _Slot):
+    def _launch(self, gr: _Graph, s: _Slot):
         torch = self.torch
-        bq = [s.queue["bfs"].popleft() for _ in range(min(GROUP, len(s.queue["bfs"])))]
-        sq = [s.queue["sssp"].popleft() for _ in range(min(GROUP, len(s.queue["sssp"])))]
-        cq = list(s.queue["cc"])
-        s.queue["cc"].clear()
-        need = s.batch_bytes(len(bq), len(sq), len(cq))
+        bq = [gr.queue["bfs"].popleft() for _ in range(min(GROUP, len(gr.queue["bfs"])))]
+        sq = [gr.queue["sssp"].popleft() for _ in range(min(GROUP, len(gr.queue["sssp"])))]
+        cq = list(gr.queue["cc"])
+        gr.queue["cc"].clear()
+        need = gr.batch_bytes(len(bq), len(sq), len(cq))
         if self._free_bytes() - need < self.reserve:
             # not admitted: back to the front of the queues, retried when memory frees up
             for q, items in (("bfs", bq), ("sssp", sq), ("cc", cq)):
-                s.queue[q].extendleft(reversed(items))
+                gr.queue[q].extendleft(reversed(items))
             self.deferred += 1
             return False
         n = s.n
+        # the slot's pinned source list is free: its previous batch has completed
+        for j, r in enumerate(bq):
+            s.h_srcs[j] = r.src
+        for j, r in enumerate(sq):
+            s.h_srcs[GROUP + j] = r.src
         with torch.cuda.stream(s.stream):
-            bufs = []
             if bq:
-                srcs = torch.tensor([r.src for r in bq], dtype=torch.int32).pin_memory()
-                out = torch.empty(len(bq) * n, dtype=torch.int32, device="cuda")
-                alb.alb_bfs_batch(s.G.h, srcs, len(bq), out, s.stream)
-                s.h_bfs[: len(bq) * n].copy_(out, non_blocking=True)
-                bufs += [srcs, out]
+                alb.alb_bfs_batch(s.G.h, s.h_srcs[:len(bq)], len(bq), s.d_bfs, s.stream)
+                s.h_bfs[: len(bq) * n].copy_(s.d_bfs[: len(bq) * n], non_blocking=True)
             if sq:
-                srcs = torch.tensor([r.src for r in sq], dtype=torch.int32).pin_memory()
-                out = torch.empty(len(sq) * n, dtype=torch.int32, device="cuda")
-                alb.alb_sssp_batch(s.G.h, srcs, len(sq), out, s.stream)
-                s.h_sssp[: len(sq) * n].copy_(out, non_blocking=True)
-                bufs += [srcs, out]
+                alb.alb_sssp_batch(s.G.h, s.h_srcs[GROUP:GROUP + len(sq)], len(sq), s.d_sssp, s.stream)
+                s.h_sssp[: len(sq) * n].copy_(s.d_sssp[: len(sq) * n], non_blocking=True)
             if cq:
-                out = torch.empty(n, dtype=torch.int32, device="cuda")
-                alb.alb_cc(s.G.h, out, s.stream)
-                s.h_cc.copy_(out, non_blocking=True)
-                bufs.append(out)
+                alb.alb_cc(s.G.h, s.d_cc, s.stream)
+                s.h_cc.copy_(s.d_cc, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(s.stream)
-        s.busy = (ev, bq, sq, cq, bufs)
+        s.busy = (ev, bq, sq, cq, None, time.perf_counter())
         self.batches += 1
         return True
 
-    def _complete(self, s: _Slot, now: float):
-        ev, bq, sq, cq, bufs = s.busy
+    def _complete(self, gr: _Graph, s: _Slot, now: float):
+        ev, bq, sq, cq, bufs, t_launch = s.busy
+        if self.checked:
+            rec = alb.alb_debug_check(s.G.h)
+            if rec[0]:
+                raise RuntimeError(f"bounds check failed on graph n={gr.n} m={gr.m} slot "
+                                   f"{gr.slots.index(s)}: code {rec[0]} index {rec[1]} bound {rec[2]} "
+                                   f"count {rec[3]}; batch bfs={len(bq)} sssp={len(sq)} cc={len(cq)}")
+        gr.log.append((time.perf_counter() - t_launch, len(bq), len(sq), len(cq)))
         n = s.n
-        self.edges += s.m * (len(bq) + len(sq) + len(cq))
+        self.edges += gr.m * (len(bq) + len(sq) + len(cq))
         for j, r in enumerate(bq):
             r.done = now
             if self.keep:
@@ -161,7 +225,6 @@ class Server:
             if self.keep:
                 self.results[r.rid] = s.h_cc.numpy().view(np.uint32).copy()
         s.busy = None
-        del bufs
 
     def run(self, requests: list[Request], *, realtime: bool = True, timeout: float = 600.0):
         """Serve `requests` (sorted by arrival). realtime=False admits everything at once
@@ -177,17 +240,18 @@ class Server:
                 r = reqs[i]
                 if not realtime:
                     r.arrival = 0.0
-                self.slots[r.graph].queue[r.kind].append(r)
+                self.graphs[r.graph].queue[r.kind].append(r)
                 i += 1
             progressed = False
-            for s in self.slots:
-                if s.busy is not None and s.busy[0].query():
-                    before = sum(len(x) for x in s.busy[1:4])
-                    self._complete(s, time.perf_counter() - t0)
-                    pending -= before
-                    progressed = True
-                if s.busy is None and any(s.queue[k] for k in KINDS):
-                    progressed |= self._launch(s)
+            for gr in self.graphs:
+                for s in gr.slots:
+                    if s.busy is not None and s.busy[0].query():
+                        before = sum(len(x) for x in s.busy[1:4])
+                        self._complete(gr, s, time.perf_counter() - t0)
+                        pending -= before
+                        progressed = True
+                    if s.busy is None and any(gr.queue[k] for k in KINDS):
+                        progressed |= self._launch(gr, s)
             if not progressed:
                 time.sleep(0.0001)
         return time.perf_counter() - t0
@@ -201,7 +265,7 @@ def one_at_a_time(graphs_or_server, requests: list[Request], *, keep_results: bo
     res = {}
     t0 = time.perf_counter()
     for r in sorted(requests, key=lambda q: q.arrival):
-        s = srv.slots[r.graph]
+        s = srv.graphs[r.graph].slots[0]
         out = torch.empty(s.n, dtype=torch.int32, device="cuda")
         if r.kind == "bfs":
             alb.alb_bfs(s.G.h, r.src, out)
@@ -214,6 +278,21 @@ def one_at_a_time(graphs_or_server, requests: list[Request], *, keep_results: bo
             res[r.rid] = h.numpy().view(np.uint32).copy()
     torch.cuda.synchronize()
     return time.perf_counter() - t0, res
+
+
+def slot_stats(server: "Server", requests: list[Request]) -> list[dict]:
+    """Per graph: latency percentiles, batches, mean batch time and size."""
+    out = []
+    for gi, s in enumerate(server.graphs):
+        rs = [r for r in requests if r.graph == gi]
+        lat = np.array([r.done - r.arrival for r in rs]) * 1e3 if rs else np.zeros(1)
+        log = np.array(s.log) if s.log else np.zeros((1, 4))
+        out.append({"graph": gi, "m": s.m, "slots": len(s.slots), "requests": len(rs),
+                    "p50_ms": round(float(np.percentile(lat, 50)), 2),
+                    "p99_ms": round(float(np.percentile(lat, 99)), 2),
+                    "batches": len(s.log), "batch_ms_mean": round(float(log[:, 0].mean() * 1e3), 2),
+                    "batch_size_mean": round(float(log[:, 1:].sum(axis=1).mean()), 1)})
+    return out
 
 
 def latency_stats(requests: list[Request]) -> dict:

@@ -22,8 +22,9 @@ def graphs():
 
 def test_results_alone_equal_results_in_the_mix(graphs):
     reqs = serve.poisson_requests(graphs, 400, rate=20000.0, seed=5)
-    srv = serve.Server(graphs, tune=False, keep_results=True)
+    srv = serve.Server(graphs, tune=False, keep_results=True, big_graph_edges=100_000)
     try:
+        assert len(srv.graphs[-1].slots) == 2            # a large graph gets a second slot (a clone)
         srv.run(reqs, realtime=True, timeout=120)
         assert all(r.done >= r.arrival for r in reqs)
         assert srv.batches < len(reqs)               # requests were batched together
@@ -49,11 +50,11 @@ def test_admission_waits_for_free_device_memory(graphs):
     srv = serve.Server(graphs, tune=False, keep_results=True)
     try:
         srv.reserve = 1 << 60                           # nothing fits
-        s = srv.slots[reqs[0].graph]
-        s.queue[reqs[0].kind].append(reqs[0])
-        assert srv._launch(s) is False and srv.deferred == 1
-        assert len(s.queue[reqs[0].kind]) == 1          # the request is still queued
-        s.queue[reqs[0].kind].clear()
+        gr = srv.graphs[reqs[0].graph]
+        gr.queue[reqs[0].kind].append(reqs[0])
+        assert srv._launch(gr, gr.slots[0]) is False and srv.deferred == 1
+        assert len(gr.queue[reqs[0].kind]) == 1         # the request is still queued
+        gr.queue[reqs[0].kind].clear()
         srv.reserve = 0
         srv.run(reqs, realtime=False, timeout=60)
         assert all(r.done >= 0 for r in reqs)

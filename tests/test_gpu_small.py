@@ -368,6 +368,14 @@ def test_batch_argument_errors(rmat13):
     assert e.value.code == 1
     with pytest.raises(alb.AlbError):
         G.bfs_multi(np.array([g.n + 5], dtype=np.uint32))
+    # device-memory sources are checked on the device: the bad one is skipped, the error latched
+    bad = torch.tensor([0, g.n + 5], dtype=torch.int32, device="cuda")
+    out = torch.empty(2 * g.n, dtype=torch.int32, device="cuda")
+    G.bfs_batch(bad, out)
+    with pytest.raises(alb.AlbError) as e:
+        G.sync()
+    assert e.value.code == 1
+    assert np.array_equal(host(out)[:g.n], oracle.bfs(g.n, g.offsets, g.indices, 0))
     G.close()
 
 
@@ -406,3 +414,25 @@ def test_per_app_params_are_independent(rmat13):
     G.sssp(src, o)
     assert G.stats()["hub_threshold"] == 0       # sssp: every vertex huge
     G.close()
+
+
+def test_clone_shares_the_csr_and_outlives_the_original(rmat13):
+    g = rmat13
+    G = make(g)
+    G.set_app_params("bfs", hub_threshold=64)
+    C = G.clone()
+    assert C.params("bfs").hub_threshold == 64
+    src = g.max_degree_vertex()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    o1 = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    o2 = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    G.bfs(src, o1, stream=s1)          # the two handles run on different streams
+    C.sssp(src, o2, stream=s2)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(o1), oracle.bfs(g.n, g.offsets, g.indices, src))
+    assert np.array_equal(host(o2), oracle.sssp(g.n, g.offsets, g.indices, g.weights, src))
+    G.close()                          # the clone keeps the CSR alive
+    C.cc(o1)
+    C.sync()
+    assert np.array_equal(host(o1), oracle.cc(g.n, g.offsets, g.indices))
+    C.close()
