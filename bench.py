@@ -59,7 +59,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["alb", "reference"], default="alb")
     ap.add_argument("--workload", choices=["rmat24-hubs", "rmat22-hubs", "rmat22", "rmat16",
-                                           "batch-sources", "batch-graphs", "ablation", "serve"],
+                                           "batch-sources", "batch-graphs", "ablation", "serve",
+                                           "cta-load"],
                     default="rmat24-hubs",
                     help="batch-*: batched vs one-query-at-a-time throughput (separate line)")
     ap.add_argument("--apps", default="", help="comma list restricting the workload's apps")
@@ -733,9 +734,61 @@ def serve_arm(args, dist):
         print(json.dumps(line), flush=True)
 
 
+def cta_load_arm(args, dist):
+    """Thread-block (CTA) load distribution, the measure of the paper's Figs. 1 and 4: edges
+    expanded by each CTA of the TWC part and of the LB kernel, summed over one call, for bfs, sssp
+    and pr on the severe-imbalance graph under TWC only (threshold above the maximum degree) and
+    ALB (the paper's rule). Reports max / mean / min per kernel and the max-over-mean imbalance."""
+    import torch
+    from paper_1911_09135_gb300 import alb
+
+    torch.cuda.set_device(dist.local)
+    alb.load()
+    g, desc, apps = workload("rmat24-hubs")
+    step = GpuStep(g, ("bfs", "sssp", "pr"), alb, torch)
+
+    def summary(x):
+        x = np.asarray(x, dtype=np.float64)
+        if x.size == 0 or x.sum() == 0:
+            return None
+        return {"ctas": int(x.size), "max": int(x.max()), "mean": round(float(x.mean()), 1),
+                "min": int(x.min()), "max_over_mean": round(float(x.max() / x.mean()), 3),
+                "p99_over_p50": round(float(np.percentile(x, 99) / max(np.percentile(x, 50), 1)), 3)}
+
+    table = {}
+    for policy, t in (("twc", 1 << 40), ("alb", -1)):
+        step.G.set_params(hub_threshold=t, cta_stats=1)
+        for a in step.apps:
+            step.run_app(a)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            step.run_app(a)
+            e1.record()
+            torch.cuda.synchronize()
+            twc, lb = step.G.cta_loads()
+            table[f"{policy}/{a}"] = {"ms": round(e0.elapsed_time(e1), 3), "twc_kernel": summary(twc),
+                                      "lb_kernel": summary(lb)}
+    step.close()
+    line = {"metric": "per-CTA edges expanded in one call (thread-block load distribution)",
+            "unit": "edges", "n_gpus": dist.world, "config": {"workload": f"{g.name}: {desc}"},
+            "table": table}
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     dist = Dist()
+    if args.workload == "cta-load":
+        import torch
+        dist.init("nccl" if torch.cuda.is_available() else "gloo")
+        try:
+            cta_load_arm(args, dist)
+        finally:
+            dist.done()
+        return
     if args.workload == "serve":
         import torch
         dist.init("nccl" if torch.cuda.is_available() else "gloo")

@@ -95,6 +95,7 @@ typedef struct {
   uint32_t max_rounds;     /* 0: n + 1 (enough for every app); ALB_ERR_TIMEOUT when reached */
   float l2_persist_fraction; /* share of L2 kept for the label array (0 = off, default) */
   uint32_t profile;        /* 1: time every kernel launch with CUDA events (host loop only) */
+  uint32_t cta_stats;      /* 1: count the edges each CTA expands (alb_get_cta_loads) */
 } alb_params;
 
 /* Counters of the last completed call on a handle. */
@@ -284,6 +285,15 @@ alb_status alb_get_stats(alb_graph g, alb_stats* out);
 
 /* Static string for a status code. */
 const char* alb_status_str(alb_status s);
+
+/* Per-CTA load of the last call made with cta_stats = 1 (the measure behind the paper's
+ * thread-block load distributions, Sec. 3 Fig. 1 and Sec. 5.1 Fig. 4): hd_twc[b] = edges CTA b of
+ * the TWC part expanded (the inspection kernel of bfs/sssp/cc/kcore; PageRank's pull kernel), and
+ * hd_lb[b] = edges CTA b of the LB kernel expanded, summed over the call's rounds. At most cap
+ * entries are written to each (host or device memory); *n_twc / *n_lb receive the number of
+ * CTAs (0 if the last call was not instrumented). Synchronises the handle's last stream. */
+alb_status alb_get_cta_loads(alb_graph g, uint64_t* hd_twc, uint64_t* hd_lb, uint32_t cap,
+                             uint32_t* n_twc, uint32_t* n_lb);
 
 /* Bounds-checked build. libalb_checked.so (built with -DALB_CHECKED) tests every CSR, frontier,
  * worklist and label-row index a round kernel uses; an index out of range is skipped and

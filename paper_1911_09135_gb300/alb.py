@@ -34,7 +34,7 @@ EXPORTS = [
     "alb_bfs_batch", "alb_sssp_batch", "alb_inspect", "alb_lb_trace", "alb_threshold_rule",
     "alb_sync", "alb_get_stats", "alb_status_str", "alb_version", "alb_bfs_noalloc",
     "alb_bfs_multi", "alb_sssp_multi", "alb_autotune", "alb_set_app_params", "alb_get_app_params",
-    "alb_graph_clone", "alb_debug_check", "alb_checked_build",
+    "alb_graph_clone", "alb_debug_check", "alb_checked_build", "alb_get_cta_loads",
 ]
 
 ALB_APP = {"bfs": 0, "sssp": 1, "cc": 2, "pr": 3, "pagerank": 3, "kcore": 4}
@@ -57,6 +57,7 @@ class alb_params(ctypes.Structure):
         ("max_rounds", ctypes.c_uint32),
         ("l2_persist_fraction", ctypes.c_float),
         ("profile", ctypes.c_uint32),
+        ("cta_stats", ctypes.c_uint32),
     ]
 
 
@@ -105,6 +106,7 @@ def load(build_if_missing: bool = False):
         "alb_graph_destroy": ([_P], S),
         "alb_graph_clone": ([_P, ctypes.POINTER(_P)], S),
         "alb_debug_check": ([_P, _P], S),
+        "alb_get_cta_loads": ([_P, _P, _P, _U32, ctypes.POINTER(_U32), ctypes.POINTER(_U32)], S),
         "alb_checked_build": ([], _U32),
         "alb_default_params": ([ctypes.POINTER(alb_params)], S),
         "alb_set_params": ([_P, ctypes.POINTER(alb_params)], S),
@@ -322,6 +324,16 @@ def alb_version() -> int:
     return int(load().alb_version())
 
 
+def alb_get_cta_loads(g, cap: int = 1 << 16):
+    """(twc, lb): per-CTA edge counts of the last cta_stats call, as uint64 arrays."""
+    twc = np.zeros(cap, dtype=np.uint64)
+    lb = np.zeros(cap, dtype=np.uint64)
+    nt, nl = _U32(0), _U32(0)
+    _check(load().alb_get_cta_loads(g, twc.ctypes.data, lb.ctypes.data, cap, ctypes.byref(nt),
+                                    ctypes.byref(nl)), "alb_get_cta_loads")
+    return twc[:min(cap, nt.value)], lb[:min(cap, nl.value)]
+
+
 def alb_checked_build() -> int:
     return int(load().alb_checked_build())
 
@@ -463,6 +475,9 @@ class Graph:
         out = self._out(out, np.uint32)
         alb_sssp_multi(self.h, srcs, _numel(srcs), out, stream)
         return out
+
+    def cta_loads(self):
+        return alb_get_cta_loads(self.h)
 
     def autotune(self, app, src=0, reps=3, stream=None):
         return alb_autotune(self.h, app, src, reps, stream)

@@ -82,6 +82,8 @@ static void free_graph_memory(alb_graph g) {
   cudaFree(g->st);
   cudaFree(g->args);
   cudaFree(g->chk);
+  cudaFree(g->cta_twc);
+  cudaFree(g->cta_lb);
   if (g->h_st) cudaFreeHost(g->h_st);
   cudaGetLastError();
 }
@@ -132,6 +134,35 @@ void select_cfg(alb_graph g, int app) {
   g->threshold = c.threshold;
 }
 
+alb_status reset_cta_loads(alb_graph g, cudaStream_t s) {
+  // counters are sized for the largest grid any application of the handle may use
+  uint32_t need = 0;
+  for (int a = 0; a < 5; ++a) {
+    need = g->cfg[a].blocks > need ? g->cfg[a].blocks : need;
+    need = g->cfg[a].lb_blocks > need ? g->cfg[a].lb_blocks : need;
+  }
+  need = need < 4096u ? 4096u : need;  // PageRank's own grids are at most SMs x 16 CTAs
+  if (g->cta_cap < need) {
+    // cached graphs hold the counters' addresses: drop them all before the arrays move
+    ALB_CUDA_TRY(cudaDeviceSynchronize());
+    free_traversal_graphs(g);
+    free_pagerank(g);
+    free_batch(g);
+    cudaFree(g->cta_twc);
+    cudaFree(g->cta_lb);
+    g->cta_twc = g->cta_lb = nullptr;
+    g->cta_cap = 0;
+    ALB_CUDA_TRY(cudaMalloc((void**)&g->cta_twc, sizeof(unsigned long long) * need));
+    ALB_CUDA_TRY(cudaMalloc((void**)&g->cta_lb, sizeof(unsigned long long) * need));
+    g->cta_cap = need;
+  }
+  ALB_CUDA_TRY(cudaMemsetAsync(g->cta_twc, 0, sizeof(unsigned long long) * g->cta_cap, s));
+  ALB_CUDA_TRY(cudaMemsetAsync(g->cta_lb, 0, sizeof(unsigned long long) * g->cta_cap, s));
+  g->cta_n_twc = g->blocks;
+  g->cta_n_lb = g->lb_blocks;
+  return ALB_OK;
+}
+
 alb_status latch_from_state(alb_graph g, uint32_t status) {
   if (status & ST_ERR_SRC) g->latched = ALB_ERR_INVALID_ARG;
   else if (status & ST_ERR_INDEX) g->latched = ALB_ERR_DEVICE;
@@ -153,6 +184,20 @@ uint32_t alb_checked_build(void) {
 #else
   return 0u;
 #endif
+}
+
+alb_status alb_get_cta_loads(alb_graph g, uint64_t* hd_twc, uint64_t* hd_lb, uint32_t cap,
+                             uint32_t* n_twc, uint32_t* n_lb) {
+  if (!g || !n_twc || !n_lb) return ALB_ERR_INVALID_ARG;
+  if (cudaSetDevice(g->device) != cudaSuccess) return ALB_ERR_CUDA;
+  ALB_CUDA_TRY(cudaStreamSynchronize(g->last_stream));
+  *n_twc = g->cta_twc ? g->cta_n_twc : 0u;
+  *n_lb = g->cta_lb ? g->cta_n_lb : 0u;
+  if (hd_twc && *n_twc)
+    ALB_CUDA_TRY(cudaMemcpy(hd_twc, g->cta_twc, sizeof(uint64_t) * (cap < *n_twc ? cap : *n_twc), cudaMemcpyDefault));
+  if (hd_lb && *n_lb)
+    ALB_CUDA_TRY(cudaMemcpy(hd_lb, g->cta_lb, sizeof(uint64_t) * (cap < *n_lb ? cap : *n_lb), cudaMemcpyDefault));
+  return ALB_OK;
 }
 
 alb_status alb_debug_check(alb_graph g, uint32_t* out4) {
@@ -199,7 +244,7 @@ alb_status alb_default_params(alb_params* p) {
 }
 
 static bool params_valid(const alb_params* p) {
-  if (p->distribution > 1 || p->exec_mode > 1 || p->profile > 1) return false;
+  if (p->distribution > 1 || p->exec_mode > 1 || p->profile > 1 || p->cta_stats > 1) return false;
   if (p->twc_warp_min > p->twc_cta_min) return false;
   if (p->grid_blocks > (1u << 20)) return false;
   if (!(p->l2_persist_fraction >= 0.f && p->l2_persist_fraction <= 1.f)) return false;
@@ -425,6 +470,7 @@ alb_status alb_get_stats(alb_graph g, alb_stats* out) {
 static alb_status begin_call(alb_graph g, int app) {
   if (cudaSetDevice(g->device) != cudaSuccess) return ALB_ERR_CUDA;
   select_cfg(g, app);
+  if (!g->params.cta_stats) g->cta_n_twc = g->cta_n_lb = 0;  // this call is not instrumented
   g->stats.ms_inspect = g->stats.ms_lb = g->stats.ms_other = 0.0;
   g->stats.n_inspect = g->stats.n_lb = g->stats.n_other = 0;
   return ALB_OK;

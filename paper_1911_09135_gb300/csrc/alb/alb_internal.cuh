@@ -77,6 +77,8 @@ struct TravCtx {
   cudaGraphConditionalHandle h_while;
   cudaGraphConditionalHandle h_if;
   uint32_t* chk;          // checked build: first failed bound (code, index, bound, count)
+  unsigned long long* cta_twc;  // per-CTA edges expanded by the TWC kernel (cta_stats; else null)
+  unsigned long long* cta_lb;   // per-CTA edges expanded by the LB kernel
 };
 
 // Codes recorded by the checked build (-DALB_CHECKED) when an index is out of range; the
@@ -132,6 +134,10 @@ struct alb_graph_s {
   alb::CallArgs* args = nullptr;
   alb::RoundState* h_st = nullptr;  // pinned mirror
   uint32_t* chk = nullptr;          // 4 words: checked-build bound failures (never reset)
+  unsigned long long* cta_twc = nullptr;  // per-CTA load counters (cta_stats)
+  unsigned long long* cta_lb = nullptr;
+  uint32_t cta_cap = 0;             // entries of each counter array
+  uint32_t cta_n_twc = 0, cta_n_lb = 0;  // CTAs of the last instrumented call
 
   cudaGraph_t graph[alb::APP_COUNT] = {};
   cudaGraphExec_t exec[alb::APP_COUNT] = {};
@@ -183,5 +189,6 @@ alb_status batch_stats(alb_graph g, alb_stats* out);
 alb_status latch_from_state(alb_graph g, uint32_t status);
 uint32_t effective_threshold(alb_graph g);
 void select_cfg(alb_graph g, int app);
+alb_status reset_cta_loads(alb_graph g, cudaStream_t s);  // zero (and size) the per-CTA counters
 
 }  // namespace alb

@@ -329,7 +329,10 @@ __global__ void __launch_bounds__(kBlock) k_inspect(TravCtx c) {
   // statistics: one atomic per warp
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) twc_edges += __shfl_down_sync(kFull, twc_edges, o);
-  if (lane == 0 && twc_edges) atomicAdd(&st->edges_twc, twc_edges);
+  if (lane == 0 && twc_edges) {
+    atomicAdd(&st->edges_twc, twc_edges);
+    if (c.cta_twc) atomicAdd(c.cta_twc + blockIdx.x, twc_edges);  // per-CTA load (cta_stats)
+  }
 
   if (last_block_ticket(&st->done_inspect)) {
     const unsigned long long hp = __ldcg(&st->hub_packed);
@@ -408,12 +411,16 @@ __global__ void __launch_bounds__(kBlock) k_lb(TravCtx c) {
   const uint64_t p = (uint64_t)gridDim.x * kBlock;
   const uint64_t gt = (uint64_t)blockIdx.x * kBlock + tid;
   constexpr int U = 4;
+  unsigned long long lb_edges = 0ull;  // positions this thread processed (cta_stats)
   auto process = [&](const uint64_t (&k)[U], const bool (&ok)[U]) {
     uint32_t ed[U], sv[U], src[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       ed[u] = 0u; sv[u] = 0u; src[u] = 0u;
-      if (ok[u]) resolve((uint32_t)k[u], ed[u], sv[u], src[u]);
+      if (ok[u]) {
+        resolve((uint32_t)k[u], ed[u], sv[u], src[u]);
+        ++lb_edges;
+      }
     }
     if constexpr (kTrace) {
 #pragma unroll
@@ -452,6 +459,11 @@ __global__ void __launch_bounds__(kBlock) k_lb(TravCtx c) {
     }
   }
 
+  if (c.cta_lb) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lb_edges += __shfl_down_sync(kFull, lb_edges, o);
+    if (lane == 0 && lb_edges) atomicAdd(c.cta_lb + blockIdx.x, lb_edges);
+  }
   if (last_block_ticket(&st->done_lb)) {
     if constexpr (!kTrace) finish_round(c);
   }

@@ -63,6 +63,8 @@ struct PrCtx {
   const uint32_t* task_len;
   const uint32_t* hub_t0;      // tasks of hub j: [hub_t0[j], hub_t0[j+1])
   float* part2;
+  unsigned long long* cta_twc; // per-CTA edges (cta_stats; else null)
+  unsigned long long* cta_lb;
   PrState* st;
   const PrArgs* args;
   cudaGraphConditionalHandle h_while;
@@ -278,6 +280,7 @@ __global__ void __launch_bounds__(kBlock) k_pr_pull(PrCtx c) {
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   double l1 = 0.0;
   float dang = 0.0f;
+  unsigned long long edges = 0ull;  // this thread's share of the CTA's load (cta_stats)
   // CTA bin: entries blockIdx.x + i * gridDim.x; every warp sums a strided slice of the
   // vertex's edges, the 8 warp sums of a batch of 32 vertices are combined after one barrier.
   const uint32_t G = gridDim.x;
@@ -301,6 +304,7 @@ __global__ void __launch_bounds__(kBlock) k_pr_pull(PrCtx c) {
         for (int w = 0; w < kWarps; ++w) t += s_part[tid][w];
         const uint32_t v = c.ctas[j];
         pr_update(c, v, c.off[v + 1] - c.off[v], t, base, d, par, l1, dang);
+        edges += c.off[v + 1] - c.off[v];
       }
     }
     __syncthreads();
@@ -311,7 +315,10 @@ __global__ void __launch_bounds__(kBlock) k_pr_pull(PrCtx c) {
     const uint32_t v = c.warps[j];
     const uint32_t b = c.off[v], deg = c.off[v + 1] - b;
     float sv = warp_sum(strided_sum<4>(idx, cb, b, deg, lane, 32));
-    if (lane == 0) pr_update(c, v, deg, sv, base, d, par, l1, dang);
+    if (lane == 0) {
+      pr_update(c, v, deg, sv, base, d, par, l1, dang);
+      edges += deg;
+    }
   }
   // thread bin: one thread per vertex, its edges in order, 8 loads in flight
   const uint32_t gt = blockIdx.x * kBlock + tid, nthreads = gridDim.x * kBlock;
@@ -319,6 +326,12 @@ __global__ void __launch_bounds__(kBlock) k_pr_pull(PrCtx c) {
     const uint32_t v = c.smalls[j];
     const uint32_t b = c.off[v], deg = c.off[v + 1] - b;
     pr_update(c, v, deg, strided_sum<8>(idx, cb, b, deg, 0, 1), base, d, par, l1, dang);
+    edges += deg;
+  }
+  if (c.cta_twc) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) edges += __shfl_down_sync(kFull, edges, o);
+    if (lane == 0 && edges) atomicAdd(c.cta_twc + blockIdx.x, edges);
   }
   block_reduce_store<kBlock>(l1, dang, c.l1_part + blockIdx.x, c.dang_part + blockIdx.x);
 }
@@ -347,6 +360,7 @@ __global__ void __launch_bounds__(kBlock) k_pr_hub(PrCtx c) {
   const uint64_t gt = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
   constexpr int U = 4;
   uint32_t j = 0u;
+  unsigned long long edges = 0ull;  // positions this thread took (cta_stats)
   for (uint64_t k0 = gt - lane; k0 < e; k0 += p * U) {  // warp-uniform
     uint32_t jj[U], id[U];
 #pragma unroll
@@ -359,6 +373,7 @@ __global__ void __launch_bounds__(kBlock) k_pr_hub(PrCtx c) {
         jj[u] = j;
         const uint32_t base = staged ? s_base[j] : c.off[c.hubs[j]] - c.hub_p[j];
         id[u] = __ldcs(c.idx + (uint32_t)k + base);
+        ++edges;
       }
     }
     float val[U];
@@ -376,6 +391,11 @@ __global__ void __launch_bounds__(kBlock) k_pr_hub(PrCtx c) {
       const bool tail = jj[u] != kInf && (lane == 31 || jn != jj[u]);
       if (tail) c.part[(uint32_t)((k0 + (uint64_t)u * p) >> 5) + jj[u]] = val[u];
     }
+  }
+  if (c.cta_lb) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) edges += __shfl_down_sync(kFull, edges, o);
+    if (lane == 0 && edges) atomicAdd(c.cta_lb + blockIdx.x, edges);
   }
 }
 
@@ -519,6 +539,8 @@ static PrCtx pr_ctx(alb_graph g, bool use_graph, cudaGraphConditionalHandle hw) 
   c.task_len = w->task_len;
   c.hub_t0 = w->hub_t0;
   c.part2 = w->part2;
+  c.cta_twc = g->params.cta_stats ? g->cta_twc : nullptr;
+  c.cta_lb = g->params.cta_stats ? g->cta_lb : nullptr;
   c.st = w->st;
   c.args = w->args;
   c.h_while = hw;
@@ -743,9 +765,18 @@ extern "C" alb_status alb_pagerank(alb_graph g, float damping, double tol, uint3
   g->stats.ms_inspect = g->stats.ms_lb = g->stats.ms_other = 0.0;
   g->stats.n_inspect = g->stats.n_lb = g->stats.n_other = 0;
   cudaStream_t s = (cudaStream_t)stream;
+  if (!g->params.cta_stats) g->cta_n_twc = g->cta_n_lb = 0;  // this call is not instrumented
+  if (g->params.cta_stats) {  // before the setup: the counters' addresses go into the cached graph
+    alb_status rc0 = reset_cta_loads(g, s);
+    if (rc0 != ALB_OK) return rc0;
+  }
   alb_status rc = pr_setup(g, s);
   if (rc != ALB_OK) return rc;
   PrWs* w = g->pr;
+  if (g->params.cta_stats) {
+    g->cta_n_twc = w->pull_blocks;
+    g->cta_n_lb = w->nh ? w->hub_blocks : 0u;
+  }
   const bool dev_rank = is_device_ptr(hd_rank);
   float* rank = hd_rank;
   if (!dev_rank) {

@@ -120,6 +120,8 @@ TravCtx make_ctx(alb_graph g, bool use_graph, cudaGraphConditionalHandle hw,
   c.h_if = hi;
   c.m = (uint32_t)g->m;
   c.chk = g->chk;
+  c.cta_twc = g->params.cta_stats ? g->cta_twc : nullptr;
+  c.cta_lb = g->params.cta_stats ? g->cta_lb : nullptr;
   return c;
 }
 
@@ -282,6 +284,10 @@ alb_status run_traversal(alb_graph g, App app, uint32_t src, uint32_t k, uint32_
   CallArgs ca{lab, src, k, nullptr, nullptr, nullptr};
   k_set_args<<<1, 1, 0, s>>>(g->args, ca);
   ALB_CUDA_TRY(cudaGetLastError());
+  if (g->params.cta_stats) {
+    alb_status rc = reset_cta_loads(g, s);
+    if (rc != ALB_OK) return rc;
+  }
   if (g->params.exec_mode == 0) {
     if (!g->exec[app]) {
       alb_status rc = build_graph(g, app);

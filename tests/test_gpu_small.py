@@ -436,3 +436,28 @@ def test_clone_shares_the_csr_and_outlives_the_original(rmat13):
     C.sync()
     assert np.array_equal(host(o1), oracle.cc(g.n, g.offsets, g.indices))
     C.close()
+
+
+def test_cta_loads_account_for_every_edge(rmat13):
+    """Per-CTA counters (the paper's thread-block load measure) sum to the edges expanded."""
+    g = rmat13
+    G = make(g)
+    src = g.max_degree_vertex()
+    o = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    G.set_params(hub_threshold=512, cta_stats=1)
+    G.bfs(src, o)
+    st = G.stats()
+    twc, lb = G.cta_loads()
+    assert len(twc) == st["grid_blocks"] and len(lb) == st["lb_threads"] // st["block_size"]
+    assert int(twc.sum()) == st["edges_twc"] and int(lb.sum()) == st["edges_lb"] > 0
+    assert np.array_equal(host(o), oracle.bfs(g.n, g.offsets, g.indices, src))
+    # the cyclic LB kernel spreads huge-vertex edges evenly: CTA loads differ by <= 256 * rounds
+    assert int(lb.max()) - int(lb.min()) <= 256 * st["hub_rounds"]
+    r = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    _, it, _ = G.pagerank(0.85, 1e-6, 1000, r)
+    twc, lb = G.cta_loads()
+    assert int(twc.sum()) + int(lb.sum()) == g.m * it
+    G.set_params(cta_stats=0)
+    G.bfs(src, o)
+    assert G.cta_loads()[0].size == 0
+    G.close()
