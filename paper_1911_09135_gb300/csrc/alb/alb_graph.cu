@@ -134,14 +134,14 @@ void select_cfg(alb_graph g, int app) {
   g->threshold = c.threshold;
 }
 
-alb_status reset_cta_loads(alb_graph g, cudaStream_t s) {
+alb_status reset_cta_loads(alb_graph g, cudaStream_t s, uint32_t min_need) {
   // counters are sized for the largest grid any application of the handle may use
-  uint32_t need = 0;
+  uint32_t need = min_need;
   for (int a = 0; a < 5; ++a) {
     need = g->cfg[a].blocks > need ? g->cfg[a].blocks : need;
     need = g->cfg[a].lb_blocks > need ? g->cfg[a].lb_blocks : need;
   }
-  need = need < 4096u ? 4096u : need;  // PageRank's own grids are at most SMs x 16 CTAs
+  need = need < 4096u ? 4096u : need;
   if (g->cta_cap < need) {
     // cached graphs hold the counters' addresses: drop them all before the arrays move
     ALB_CUDA_TRY(cudaDeviceSynchronize());

@@ -189,6 +189,7 @@ alb_status batch_stats(alb_graph g, alb_stats* out);
 alb_status latch_from_state(alb_graph g, uint32_t status);
 uint32_t effective_threshold(alb_graph g);
 void select_cfg(alb_graph g, int app);
-alb_status reset_cta_loads(alb_graph g, cudaStream_t s);  // zero (and size) the per-CTA counters
+// zero (and size, to at least min_need CTAs) the per-CTA counters
+alb_status reset_cta_loads(alb_graph g, cudaStream_t s, uint32_t min_need = 0);
 
 }  // namespace alb

@@ -7,8 +7,11 @@
 //     consecutive positions and reduces them per source vertex, writing one
 //     partial per (32-position chunk, vertex) pair into its own slot; a second
 //     kernel sums each vertex's partials in chunk order;
-//   - CTA / warp / thread bins: one CTA / warp / thread forms a vertex's sum.
-// All sums have a fixed order, so the result is bit-reproducible. Values and
+//   - CTA / warp / thread bins: one CTA / warp / thread forms a vertex's sum. Each bin is cut
+//     into one contiguous range per CTA of the pull kernel with equal cost (degree + a per-vertex
+//     constant), computed once per graph, so every CTA takes the same share of every bin and no
+//     CTA is a straggler.
+// All sums have a fixed order and the assignment is static, so the result is bit-reproducible. Values and
 // sums are FP32; the L1 change that decides convergence is summed in FP64.
 //
 // Recurrence (N = n, deg = out-degree, D_t = mass on degree-0 vertices):
@@ -23,6 +26,11 @@ namespace alb {
 constexpr uint32_t kPartChunk = 4096;  // vertices per CTA in the stable partition
 constexpr uint32_t kFinTask = 4096;    // hub partial slots per first-level reduction task
 constexpr uint32_t kFinDirect = 256;   // shorter slot runs are summed by the hub's own warp
+constexpr uint32_t kPullItemCost = 3;  // per-vertex work of the pull in edge units (row bounds, x, x and x/deg stores)
+constexpr uint32_t kCutPer = 16;       // items per thread in the cost scan of the CTA cut
+constexpr uint32_t kCutChunk = kBlock * kCutPer;
+constexpr uint32_t kPullWaves = 8;     // pull CTAs = resident CTAs x this: the block scheduler then
+                                       // evens out the SMs' finishing times
 
 struct PrState {
   uint32_t iter;
@@ -50,6 +58,7 @@ struct PrCtx {
   const uint32_t* ctas;
   const uint32_t* warps;
   const uint32_t* smalls;
+  const uint32_t* pull_cut;    // bin k's range of pull CTA b: items [cut[k(G+1)+b], cut[k(G+1)+b+1])
   const uint32_t* hub_p;       // exclusive prefix of hub degrees (nh + 1)
   uint32_t e;                  // hub edges
   float* x[2];
@@ -65,6 +74,7 @@ struct PrCtx {
   float* part2;
   unsigned long long* cta_twc; // per-CTA edges (cta_stats; else null)
   unsigned long long* cta_lb;
+  uint32_t cta_cap;            // entries of each counter array
   PrState* st;
   const PrArgs* args;
   cudaGraphConditionalHandle h_while;
@@ -91,6 +101,7 @@ struct PrWs {
   uint32_t* task_len = nullptr;
   uint32_t* hub_t0 = nullptr;
   float* part2 = nullptr;
+  uint32_t* pull_cut = nullptr;
   alb::PrState* st = nullptr;
   alb::PrState* h_st = nullptr;
   alb::PrArgs* args = nullptr;
@@ -187,6 +198,121 @@ __global__ void k_pr_hub_prefix(const uint32_t* off, const uint32_t* hubs, uint3
   if (threadIdx.x == 0) prefix[nh] = s_carry;
 }
 
+// ---- one-time cost-balanced cut of the non-hub vertices over the pull kernel's CTAs
+
+__device__ __forceinline__ unsigned long long warp_incl_scan_u64(unsigned long long x) {
+  const uint32_t lane = lane_id();
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(kFull, x, o);
+    if (lane >= (uint32_t)o) x += y;
+  }
+  return x;
+}
+
+// Exclusive scan over the CTA (every thread calls it); *total receives the CTA sum.
+__device__ __forceinline__ unsigned long long block_excl_scan_u64(unsigned long long x, unsigned long long* total) {
+  __shared__ unsigned long long s_w[kWarps + 1];
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  const unsigned long long incl = warp_incl_scan_u64(x);
+  if (lane == 31) s_w[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned long long t = lane < (uint32_t)kWarps ? s_w[lane] : 0ull;
+    const unsigned long long ti = warp_incl_scan_u64(t);
+    if (lane < (uint32_t)kWarps) s_w[lane] = ti - t;
+    if (lane == 31) s_w[kWarps] = ti;
+  }
+  __syncthreads();
+  const unsigned long long r = s_w[warp] + incl - x;
+  *total = s_w[kWarps];
+  __syncthreads();
+  return r;
+}
+
+// Cost of non-hub item i (degree + kPullItemCost) and its inclusive prefix within its chunk of
+// kCutChunk items; chunk sums to csum.
+__global__ void __launch_bounds__(kBlock) k_pr_cost_scan(const uint32_t* off, const uint32_t* items, uint32_t nn,
+                                                         unsigned long long* pre, unsigned long long* csum) {
+  const uint64_t i0 = (uint64_t)blockIdx.x * kCutChunk + (uint64_t)threadIdx.x * kCutPer;
+  uint32_t cost[kCutPer];
+  unsigned long long sum = 0ull;
+#pragma unroll
+  for (uint32_t u = 0; u < kCutPer; ++u) {
+    const uint64_t i = i0 + u;
+    cost[u] = 0u;
+    if (i < nn) {
+      const uint32_t v = items[i];
+      cost[u] = off[v + 1] - off[v] + kPullItemCost;
+    }
+    sum += cost[u];
+  }
+  unsigned long long tot;
+  unsigned long long run = block_excl_scan_u64(sum, &tot);
+#pragma unroll
+  for (uint32_t u = 0; u < kCutPer; ++u) {
+    run += cost[u];
+    if (i0 + u < nn) pre[i0 + u] = run;
+  }
+  if (threadIdx.x == 0) csum[blockIdx.x] = tot;
+}
+
+// Exclusive scan of the chunk sums (one CTA, carried); coff[nchunk] = total cost.
+__global__ void __launch_bounds__(kBlock) k_pr_scan_chunks(const unsigned long long* csum, uint32_t nchunk,
+                                                           unsigned long long* coff) {
+  __shared__ unsigned long long s_carry;
+  if (threadIdx.x == 0) s_carry = 0ull;
+  __syncthreads();
+  for (uint32_t b0 = 0; b0 < nchunk; b0 += kBlock) {
+    const uint32_t b = b0 + threadIdx.x;
+    unsigned long long tot;
+    const unsigned long long ex = block_excl_scan_u64(b < nchunk ? csum[b] : 0ull, &tot);
+    if (b < nchunk) coff[b] = s_carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) coff[nchunk] = s_carry;
+}
+
+__device__ __forceinline__ unsigned long long cost_before(const unsigned long long* pre,
+                                                          const unsigned long long* coff, uint32_t i) {
+  return i == 0 ? 0ull : coff[(i - 1) / kCutChunk] + pre[i - 1];
+}
+
+// For bin k (items [s_k, e_k): CTA bin, warp bin, thread bin) and b = 0..G,
+// cut[k(G+1) + b] = number of items whose inclusive cost prefix is <= P(s_k) + floor(C_k * b / G)
+// (P = exclusive prefix, C_k = the bin's cost): CTA b takes the bin's items whose cost ends in
+// (T_b, T_{b+1}], so its share of every bin is within one item's cost of C_k / G.
+__global__ void __launch_bounds__(kBlock) k_pr_cuts(const unsigned long long* pre, const unsigned long long* coff,
+                                                    uint32_t nchunk, uint32_t nn, uint32_t nc, uint32_t nw,
+                                                    uint32_t G, uint32_t* cut) {
+  const uint32_t t = blockIdx.x * kBlock + threadIdx.x;
+  if (t >= 3u * (G + 1u)) return;
+  const uint32_t k = t / (G + 1u), b = t - k * (G + 1u);
+  const uint32_t s_k = k == 0 ? 0u : (k == 1 ? nc : nc + nw);
+  const uint32_t e_k = k == 0 ? nc : (k == 1 ? nc + nw : nn);
+  const unsigned long long P0 = cost_before(pre, coff, s_k), Ck = cost_before(pre, coff, e_k) - P0;
+  const unsigned long long T = P0 + (Ck / G) * b + ((Ck % G) * b) / G;
+  if (b == 0) { cut[t] = s_k; return; }
+  if (b == G) { cut[t] = e_k; return; }
+  const unsigned long long total = coff[nchunk];
+  if (T >= total) { cut[t] = nn; return; }
+  uint32_t lo = 0, hi = nchunk;  // largest chunk k with coff[k] <= T (coff[0] = 0 <= T < coff[nchunk])
+  while (hi - lo > 1) {
+    const uint32_t mid = lo + ((hi - lo) >> 1);
+    if (coff[mid] <= T) lo = mid; else hi = mid;
+  }
+  const unsigned long long r = T - coff[lo];
+  uint32_t a = lo * kCutChunk;  // first item of the chunk whose in-chunk prefix exceeds r
+  uint32_t z = (uint64_t)(lo + 1) * kCutChunk < nn ? (lo + 1) * kCutChunk : nn;
+  while (a < z) {
+    const uint32_t mid = a + ((z - a) >> 1);
+    if (pre[mid] <= r) a = mid + 1; else z = mid;
+  }
+  cut[t] = a;
+}
+
 // ---- iteration kernels
 
 __global__ void __launch_bounds__(kBlock) k_pr_init(PrCtx c, float dangling0) {
@@ -266,8 +392,9 @@ __device__ __forceinline__ float strided_sum(const uint32_t* __restrict__ idx, c
 
 constexpr uint32_t kCtaBatch = 32;  // CTA-bin vertices per barrier
 
-// CTA, warp and thread bins. Static assignment (entry j of a bin always goes to the same
-// CTA / warp / thread), fixed reduction order, so sums and partials are reproducible.
+// CTA, warp and thread bins. Static assignment (CTA b always takes the same cost-balanced range
+// of items, and within it the same warp / thread takes the same vertex), fixed reduction order,
+// so sums and partials are reproducible.
 __global__ void __launch_bounds__(kBlock) k_pr_pull(PrCtx c) {
   __shared__ float s_part[kCtaBatch][kWarps + 1];
   const PrArgs* pa = c.args;
@@ -281,15 +408,20 @@ __global__ void __launch_bounds__(kBlock) k_pr_pull(PrCtx c) {
   double l1 = 0.0;
   float dang = 0.0f;
   unsigned long long edges = 0ull;  // this thread's share of the CTA's load (cta_stats)
-  // CTA bin: entries blockIdx.x + i * gridDim.x; every warp sums a strided slice of the
-  // vertex's edges, the 8 warp sums of a batch of 32 vertices are combined after one barrier.
-  const uint32_t G = gridDim.x;
-  for (uint32_t q = blockIdx.x; q < c.nc; q += G * kCtaBatch) {
+  // this CTA's range of each bin (bins back to back: CTA bin [0, nc), warp bin [nc, nc + nw),
+  // thread bin after)
+  const uint32_t* items = c.ctas;
+  const uint32_t* cut = c.pull_cut + blockIdx.x;
+  const uint32_t G1 = gridDim.x + 1u;
+  // CTA bin: every warp sums a strided slice of a vertex's edges; the 8 warp sums of each of a
+  // batch of 32 vertices are combined after one barrier
+  const uint32_t c_end = cut[1];
+  for (uint32_t q = cut[0]; q < c_end; q += kCtaBatch) {
 #pragma unroll 1
     for (uint32_t i = 0; i < kCtaBatch; ++i) {
-      const uint32_t j = q + i * G;
-      if (j >= c.nc) break;  // CTA-uniform
-      const uint32_t v = c.ctas[j];
+      const uint32_t j = q + i;
+      if (j >= c_end) break;  // CTA-uniform
+      const uint32_t v = items[j];
       const uint32_t b = c.off[v], deg = c.off[v + 1] - b;
       float sv = strided_sum<4>(idx, cb, b, deg, tid, kBlock);
       sv = warp_sum(sv);
@@ -297,22 +429,23 @@ __global__ void __launch_bounds__(kBlock) k_pr_pull(PrCtx c) {
     }
     __syncthreads();
     if (tid < kCtaBatch) {
-      const uint32_t j = q + tid * G;
-      if (j < c.nc) {
+      const uint32_t j = q + tid;
+      if (j < c_end) {
         float t = 0.0f;
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) t += s_part[tid][w];
-        const uint32_t v = c.ctas[j];
-        pr_update(c, v, c.off[v + 1] - c.off[v], t, base, d, par, l1, dang);
-        edges += c.off[v + 1] - c.off[v];
+        const uint32_t v = items[j];
+        const uint32_t deg = c.off[v + 1] - c.off[v];
+        pr_update(c, v, deg, t, base, d, par, l1, dang);
+        edges += deg;
       }
     }
     __syncthreads();
   }
   // warp bin: one warp per vertex
-  const uint32_t gw = blockIdx.x * kWarps + warp, nwarps = gridDim.x * kWarps;
-  for (uint32_t j = gw; j < c.nw; j += nwarps) {
-    const uint32_t v = c.warps[j];
+  const uint32_t w_end = cut[G1 + 1];
+  for (uint32_t j = cut[G1] + warp; j < w_end; j += kWarps) {
+    const uint32_t v = items[j];
     const uint32_t b = c.off[v], deg = c.off[v + 1] - b;
     float sv = warp_sum(strided_sum<4>(idx, cb, b, deg, lane, 32));
     if (lane == 0) {
@@ -321,9 +454,9 @@ __global__ void __launch_bounds__(kBlock) k_pr_pull(PrCtx c) {
     }
   }
   // thread bin: one thread per vertex, its edges in order, 8 loads in flight
-  const uint32_t gt = blockIdx.x * kBlock + tid, nthreads = gridDim.x * kBlock;
-  for (uint32_t j = gt; j < c.ns; j += nthreads) {
-    const uint32_t v = c.smalls[j];
+  const uint32_t t_end = cut[2 * G1 + 1];
+  for (uint32_t j = cut[2 * G1] + tid; j < t_end; j += kBlock) {
+    const uint32_t v = items[j];
     const uint32_t b = c.off[v], deg = c.off[v + 1] - b;
     pr_update(c, v, deg, strided_sum<8>(idx, cb, b, deg, 0, 1), base, d, par, l1, dang);
     edges += deg;
@@ -331,7 +464,7 @@ __global__ void __launch_bounds__(kBlock) k_pr_pull(PrCtx c) {
   if (c.cta_twc) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) edges += __shfl_down_sync(kFull, edges, o);
-    if (lane == 0 && edges) atomicAdd(c.cta_twc + blockIdx.x, edges);
+    if (lane == 0 && edges && blockIdx.x < c.cta_cap) atomicAdd(c.cta_twc + blockIdx.x, edges);
   }
   block_reduce_store<kBlock>(l1, dang, c.l1_part + blockIdx.x, c.dang_part + blockIdx.x);
 }
@@ -395,7 +528,7 @@ __global__ void __launch_bounds__(kBlock) k_pr_hub(PrCtx c) {
   if (c.cta_lb) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) edges += __shfl_down_sync(kFull, edges, o);
-    if (lane == 0 && edges) atomicAdd(c.cta_lb + blockIdx.x, edges);
+    if (lane == 0 && edges && blockIdx.x < c.cta_cap) atomicAdd(c.cta_lb + blockIdx.x, edges);
   }
 }
 
@@ -507,6 +640,7 @@ alb_status free_pagerank(alb_graph g) {
   cudaFree(w->x0); cudaFree(w->x1); cudaFree(w->c0); cudaFree(w->c1);
   cudaFree(w->part); cudaFree(w->l1_part); cudaFree(w->dang_part);
   cudaFree(w->task_start); cudaFree(w->task_len); cudaFree(w->hub_t0); cudaFree(w->part2);
+  cudaFree(w->pull_cut);
   cudaFree(w->st); cudaFree(w->args); cudaFree(w->tmp_rank);
   if (w->h_st) cudaFreeHost(w->h_st);
   cudaGetLastError();
@@ -526,6 +660,7 @@ static PrCtx pr_ctx(alb_graph g, bool use_graph, cudaGraphConditionalHandle hw) 
   c.ctas = w->lists + w->nh;
   c.warps = w->lists + w->nh + w->nc;
   c.smalls = w->lists + w->nh + w->nc + w->nw;
+  c.pull_cut = w->pull_cut;
   c.hub_p = w->hub_p;
   c.e = w->e;
   c.x[0] = w->x0; c.x[1] = w->x1;
@@ -541,11 +676,27 @@ static PrCtx pr_ctx(alb_graph g, bool use_graph, cudaGraphConditionalHandle hw) 
   c.part2 = w->part2;
   c.cta_twc = g->params.cta_stats ? g->cta_twc : nullptr;
   c.cta_lb = g->params.cta_stats ? g->cta_lb : nullptr;
+  c.cta_cap = g->cta_cap;
   c.st = w->st;
   c.args = w->args;
   c.h_while = hw;
   c.use_graph = use_graph ? 1u : 0u;
   return c;
+}
+
+// Grids of the pull and hub kernels. The pull kernel needs little shared memory: the rest of the
+// SM's on-chip memory goes to L1, which caches the popular entries of the x/deg gathers. The hub
+// kernel is persistent (one wave); the pull kernel runs kPullWaves waves of its static ranges.
+static alb_status pr_grids(alb_graph g, uint32_t* pull, uint32_t* hub) {
+  ALB_CUDA_TRY(cudaFuncSetAttribute(k_pr_pull, cudaFuncAttributePreferredSharedMemoryCarveout, 5));
+  int occ = 0;
+  ALB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pr_pull, kBlock, 0));
+  *pull = g->params.grid_blocks ? g->params.grid_blocks
+                                : (uint32_t)g->num_sms * (uint32_t)(occ > 0 ? occ : 1) * kPullWaves;
+  occ = 0;
+  ALB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pr_hub, kBlock, 0));
+  *hub = g->params.grid_blocks ? g->params.grid_blocks : (uint32_t)g->num_sms * (uint32_t)(occ > 0 ? occ : 1);
+  return ALB_OK;
 }
 
 // One-time setup per graph and parameters: bins, hub prefix, buffers.
@@ -581,16 +732,31 @@ static alb_status pr_setup(alb_graph g, cudaStream_t s) {
   ALB_CUDA_TRY(cudaStreamSynchronize(s));
   const size_t slots = (size_t)(w->e / 32u) + 1 + w->nh;
   ALB_CUDA_TRY(cudaMalloc((void**)&w->part, sizeof(float) * slots));
-  // the pull kernel needs little shared memory: give the rest of the SM's on-chip memory to L1,
-  // which caches the popular entries of the x/deg gathers
-  ALB_CUDA_TRY(cudaFuncSetAttribute(k_pr_pull, cudaFuncAttributePreferredSharedMemoryCarveout, 5));
-  // grids: every PageRank kernel is persistent, sized by its own residency
-  int occ = 0;
-  ALB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pr_pull, kBlock, 0));
-  w->pull_blocks = g->params.grid_blocks ? g->params.grid_blocks : (uint32_t)g->num_sms * (uint32_t)(occ > 0 ? occ : 1);
-  ALB_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pr_hub, kBlock, 0));
-  w->hub_blocks = g->params.grid_blocks ? g->params.grid_blocks : (uint32_t)g->num_sms * (uint32_t)(occ > 0 ? occ : 1);
+  {
+    alb_status rg = pr_grids(g, &w->pull_blocks, &w->hub_blocks);
+    if (rg != ALB_OK) return rg;
+  }
   ALB_CUDA_TRY(cudaMalloc((void**)&w->l1_part, sizeof(double) * ((size_t)w->pull_blocks + w->nh)));
+  // cost-balanced cut of the non-hub items over the pull CTAs (scratch freed before returning)
+  {
+    const uint32_t nn = n - w->nh;
+    const uint32_t nchunk = (uint32_t)(((uint64_t)nn + kCutChunk - 1) / kCutChunk);
+    ALB_CUDA_TRY(cudaMalloc((void**)&w->pull_cut, sizeof(uint32_t) * 3 * ((size_t)w->pull_blocks + 1)));
+    unsigned long long* scratch = nullptr;
+    ALB_CUDA_TRY(cudaMalloc((void**)&scratch, sizeof(unsigned long long) * ((size_t)nn + 2 * (size_t)nchunk + 1)));
+    unsigned long long* pre = scratch;
+    unsigned long long* csum = scratch + nn;
+    unsigned long long* coff = csum + nchunk;
+    if (nchunk) k_pr_cost_scan<<<nchunk, kBlock, 0, s>>>(g->off, w->lists + w->nh, nn, pre, csum);
+    k_pr_scan_chunks<<<1, kBlock, 0, s>>>(csum, nchunk, coff);
+    const uint32_t ncut = 3u * (w->pull_blocks + 1u);
+    k_pr_cuts<<<(ncut + kBlock - 1) / kBlock, kBlock, 0, s>>>(pre, coff, nchunk, nn, w->nc, w->nw,
+                                                              w->pull_blocks, w->pull_cut);
+    const cudaError_t e1 = cudaGetLastError();
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaFree(scratch);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) return ALB_ERR_CUDA;
+  }
   ALB_CUDA_TRY(cudaMalloc((void**)&w->dang_part, sizeof(float) * ((size_t)w->pull_blocks + w->nh)));
   // hub-sum tasks: each hub's slot run [w0 + j, w1 + j] cut into pieces of <= kFinTask slots;
   // runs of <= kFinDirect slots are summed directly by the hub's warp
@@ -669,13 +835,16 @@ static alb_status pr_build_graph(alb_graph g) {
   wp.conditional.size = 1;
   if (cudaGraphAddNode(&n_while, G, &n_init, nullptr, 1, &wp) != cudaSuccess) return fail(ALB_ERR_CUDA);
   cudaGraph_t body = wp.conditional.phGraph_out[0];
+  // the hub branch (LB kernel and its sums) reads only x_t and writes only the hubs' entries and
+  // slots, so it runs beside the pull kernel and fills its tail; both join before the finalize
   if ((rc = pr_add_kernel(&n_pull, body, nullptr, 0, (void*)k_pr_pull, w->pull_blocks, a_c)) != ALB_OK)
     return fail(rc);
-  cudaGraphNode_t last = n_pull;
+  cudaGraphNode_t joins[2] = {n_pull, nullptr};
+  size_t njoin = 1;
   if (w->nh) {
-    if ((rc = pr_add_kernel(&n_hub, body, &last, 1, (void*)k_pr_hub, w->hub_blocks, a_c)) != ALB_OK)
+    if ((rc = pr_add_kernel(&n_hub, body, nullptr, 0, (void*)k_pr_hub, w->hub_blocks, a_c)) != ALB_OK)
       return fail(rc);
-    last = n_hub;
+    cudaGraphNode_t last = n_hub;
     if (w->ntask) {
       cudaGraphNode_t n_fin1;
       const uint32_t b1 = w->ntask < w->pull_blocks ? w->ntask : w->pull_blocks;
@@ -685,9 +854,9 @@ static alb_status pr_build_graph(alb_graph g) {
     }
     if ((rc = pr_add_kernel(&n_fin, body, &last, 1, (void*)k_pr_hub_fin, pr_fin_blocks(w), a_c)) != ALB_OK)
       return fail(rc);
-    last = n_fin;
+    joins[njoin++] = n_fin;
   }
-  if ((rc = pr_add_kernel(&n_final, body, &last, 1, (void*)k_pr_finalize, 1, a_c)) != ALB_OK)
+  if ((rc = pr_add_kernel(&n_final, body, joins, njoin, (void*)k_pr_finalize, 1, a_c)) != ALB_OK)
     return fail(rc);
   if ((rc = pr_add_kernel(&n_out, G, &n_while, 1, (void*)k_pr_output, g->blocks, a_c)) != ALB_OK)
     return fail(rc);
@@ -767,7 +936,10 @@ extern "C" alb_status alb_pagerank(alb_graph g, float damping, double tol, uint3
   cudaStream_t s = (cudaStream_t)stream;
   if (!g->params.cta_stats) g->cta_n_twc = g->cta_n_lb = 0;  // this call is not instrumented
   if (g->params.cta_stats) {  // before the setup: the counters' addresses go into the cached graph
-    alb_status rc0 = reset_cta_loads(g, s);
+    uint32_t pull = 0, hub = 0;
+    alb_status rc0 = g->pr && g->pr->ready ? ALB_OK : pr_grids(g, &pull, &hub);
+    if (rc0 == ALB_OK && g->pr && g->pr->ready) { pull = g->pr->pull_blocks; hub = g->pr->hub_blocks; }
+    if (rc0 == ALB_OK) rc0 = reset_cta_loads(g, s, pull > hub ? pull : hub);
     if (rc0 != ALB_OK) return rc0;
   }
   alb_status rc = pr_setup(g, s);

@@ -438,6 +438,30 @@ def test_clone_shares_the_csr_and_outlives_the_original(rmat13):
     C.close()
 
 
+def pull_cut_edges(g, t, wmin, cmin, nblocks, item_cost=3):
+    """Edges per CTA of the PageRank pull under its static cut: every bin (CTA, warp, thread; each
+    in vertex order) is cut separately, item cost degree + item_cost, and CTA b takes the bin's
+    items whose inclusive cost prefix lies in (T_b, T_{b+1}], T_b = P0 + floor(C * b / G)."""
+    deg = np.diff(g.offsets.astype(np.int64))
+    hub = deg >= t
+    cta = ~hub & (deg >= cmin)
+    warp = ~hub & ~cta & (deg >= wmin)
+    thr = ~hub & ~cta & ~warp
+    out = np.zeros(nblocks, dtype=np.uint64)
+    b = np.arange(nblocks + 1, dtype=np.int64)
+    for sel in (cta, warp, thr):
+        d = deg[np.flatnonzero(sel)]
+        if d.size == 0:
+            continue
+        incl = np.cumsum(d + item_cost)
+        C = int(incl[-1])
+        T = (C // nblocks) * b + ((C % nblocks) * b) // nblocks
+        cut = np.searchsorted(incl, T, side="right")
+        e = np.concatenate([[0], np.cumsum(d)])
+        out += (e[cut[1:]] - e[cut[:-1]]).astype(np.uint64)
+    return out
+
+
 def test_cta_loads_account_for_every_edge(rmat13):
     """Per-CTA counters (the paper's thread-block load measure) sum to the edges expanded."""
     g = rmat13
@@ -457,6 +481,10 @@ def test_cta_loads_account_for_every_edge(rmat13):
     _, it, _ = G.pagerank(0.85, 1e-6, 1000, r)
     twc, lb = G.cta_loads()
     assert int(twc.sum()) + int(lb.sum()) == g.m * it
+    # the pull kernel's CTAs take the cost-balanced contiguous ranges, counted per iteration
+    p = G.params()
+    exp = pull_cut_edges(g, 512, p.twc_warp_min, p.twc_cta_min, len(twc))
+    assert np.array_equal(twc, exp * it)
     G.set_params(cta_stats=0)
     G.bfs(src, o)
     assert G.cta_loads()[0].size == 0
