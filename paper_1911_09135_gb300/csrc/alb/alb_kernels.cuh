@@ -100,12 +100,43 @@ struct aggregates { static constexpr bool value = false; };
 template <class Op>
 struct aggregates<Op, decltype(void(Op::kAggregate))> { static constexpr bool value = Op::kAggregate; };
 
+// CTA-level aggregation of the counted updates (k-core) to high-degree targets. The graph's
+// hubs receive most of the decrements (every small vertex has edges to them), and same-address
+// atomics serialise in L2; warp aggregation rarely finds two lanes on the same hub. A CTA keeps
+// an open-addressing table (key = target, value = pending count) in shared memory for targets
+// whose remaining degree is >= kHotDeg and applies it with one atomic per target at the end of
+// its round. A full probe window falls back to the direct atomic. k-core's result (the k-core)
+// does not depend on the order of the decrements.
+constexpr uint32_t kHotBits = 10;
+constexpr uint32_t kHotSlots = 1u << kHotBits;
+constexpr uint32_t kHotProbe = 4;
+constexpr uint32_t kHotDeg = 1u << 16;
+static_assert(kHotSlots % kBlock == 0, "the table flush loop needs a uniform trip count");
+
+__device__ __forceinline__ bool hot_add(uint32_t* key, uint32_t* cnt, uint32_t v, uint32_t n) {
+  uint32_t s = (v * 2654435761u) >> (32 - kHotBits);
+  for (uint32_t p = 0; p < kHotProbe; ++p, s = (s + 1u) & (kHotSlots - 1u)) {
+    uint32_t k = ((volatile uint32_t*)key)[s];
+    if (k == kInf) {
+      k = atomicCAS(key + s, kInf, v);
+      if (k == kInf) k = v;
+    }
+    if (k == v) {
+      atomicAdd(cnt + s, n);
+      return true;
+    }
+  }
+  return false;
+}
+
 // Relax U edges per thread; all loads are issued before the atomics so each
 // thread keeps U independent memory requests in flight. Warp-uniform callers.
+// hot_key / hot_cnt: the CTA's aggregation table (counted operators; null = none).
 template <class Op, int U>
 __device__ __forceinline__ void relax(const TravCtx& c, const OpArgs& a, const uint32_t (&e)[U],
                                       const bool (&ok_in)[U], const uint32_t (&sv)[U], uint32_t* Fn,
-                                      uint32_t* ncount) {
+                                      uint32_t* ncount, uint32_t* hot_key = nullptr,
+                                      uint32_t* hot_cnt = nullptr) {
   uint32_t dst[U], wt[U];
   bool ok[U];
 #pragma unroll
@@ -135,7 +166,11 @@ __device__ __forceinline__ void relax(const TravCtx& c, const OpArgs& a, const u
       bool push = false;
       if (w) {
         const unsigned grp = __match_any_sync(wm, dst[u]);
-        if ((int)lane == __ffs(grp) - 1) push = Op::commit_n(a, dst[u], (uint32_t)__popc(grp));
+        if ((int)lane == __ffs(grp) - 1) {
+          const uint32_t cnt = (uint32_t)__popc(grp);
+          if (!(hot_key && cur[u] >= kHotDeg && hot_add(hot_key, hot_cnt, dst[u], cnt)))
+            push = Op::commit_n(a, dst[u], cnt);
+        }
       }
       warp_append(push, dst[u], Fn, ncount, c.n, c.chk);
     }
@@ -217,6 +252,14 @@ __global__ void __launch_bounds__(kBlock) k_inspect(TravCtx c) {
   __shared__ uint32_t s_scan[kBlock + 1], s_sb[kBlock], s_sv[kBlock];  // thread bin
   __shared__ uint32_t s_warp[kWarps + 1];
   __shared__ uint32_t s_ncta, s_nwrp, s_tile;
+  constexpr bool kHot = aggregates<Op>::value;
+  constexpr uint32_t kHotN = kHot ? kHotSlots : 1u;
+  __shared__ uint32_t s_hkey[kHotN], s_hcnt[kHotN];  // counted operators: CTA aggregation table
+  uint32_t* hk = kHot ? s_hkey : nullptr;
+  uint32_t* hc = kHot ? s_hcnt : nullptr;
+  if constexpr (kHot) {
+    for (uint32_t i = threadIdx.x; i < kHotSlots; i += kBlock) { s_hkey[i] = kInf; s_hcnt[i] = 0u; }
+  }  // visible after the tile loop's first barrier
 
   RoundState* st = c.st;
   const uint32_t r = st->round;
@@ -285,7 +328,7 @@ __global__ void __launch_bounds__(kBlock) k_inspect(TravCtx c) {
           const uint32_t q = e0 + u * kBlock + tid;
           ok[u] = q < d; e[u] = b + q; s4[u] = svj;
         }
-        relax<Op, 4>(c, a, e, ok, s4, Fn, ncount);
+        relax<Op, 4>(c, a, e, ok, s4, Fn, ncount, hk, hc);
       }
     }
     // Warp bin: one warp per vertex.
@@ -300,7 +343,7 @@ __global__ void __launch_bounds__(kBlock) k_inspect(TravCtx c) {
           const uint32_t q = e0 + u * 32 + lane;
           ok[u] = q < d; e[u] = b + q; s4[u] = svj;
         }
-        relax<Op, 4>(c, a, e, ok, s4, Fn, ncount);
+        relax<Op, 4>(c, a, e, ok, s4, Fn, ncount, hk, hc);
       }
     }
     // Thread bin: the small vertices' edges, gathered over the whole CTA
@@ -321,9 +364,18 @@ __global__ void __launch_bounds__(kBlock) k_inspect(TravCtx c) {
           s2[u] = s_sv[owner];
         }
       }
-      relax<Op, 2>(c, a, e, ok, s2, Fn, ncount);
+      relax<Op, 2>(c, a, e, ok, s2, Fn, ncount, hk, hc);
     }
     __syncthreads();
+  }
+  if constexpr (kHot) {
+    // apply the CTA's pending counts: one atomic per target; the one that crosses k pushes it
+    __syncthreads();
+    for (uint32_t i = tid; i < kHotSlots; i += kBlock) {  // same trip count in every thread
+      const uint32_t v = s_hkey[i];
+      const bool push = v != kInf && ALB_IN_RANGE(c.chk, CHK_DST, v, c.n) && Op::commit_n(a, v, s_hcnt[i]);
+      warp_append(push, v, Fn, ncount, c.n, c.chk);
+    }
   }
 
   // statistics: one atomic per warp

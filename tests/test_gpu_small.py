@@ -489,3 +489,19 @@ def test_cta_loads_account_for_every_edge(rmat13):
     G.bfs(src, o)
     assert G.cta_loads()[0].size == 0
     G.close()
+
+
+def test_kcore_hub_decrements_aggregated_per_cta():
+    """k-core on a graph whose hubs (degree > 2^16) take most decrements: the CTA-level
+    aggregation of counted updates to such targets keeps the core exact, for several k, in the
+    graph mode and in the host-loop mode, at the default threshold and with every vertex huge."""
+    g = gg.rmat(17, 16 << 17, 31, symmetrize=True, n_hubs=6, hub_degree=100000)
+    assert int(np.diff(g.offsets.astype(np.int64)).max()) >= 1 << 16
+    G = make(g)
+    o = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    for params in (dict(), dict(exec_mode=1), dict(hub_threshold=1 << 40), dict(hub_threshold=0)):
+        G.set_params(**{"hub_threshold": -1, "exec_mode": 0, **params})
+        for k in (2, 16, 40):
+            G.kcore(k, o)
+            assert np.array_equal(host(o), oracle.kcore(g.n, g.offsets, g.indices, k)), (params, k)
+    G.close()
