@@ -491,17 +491,33 @@ def test_cta_loads_account_for_every_edge(rmat13):
     G.close()
 
 
-def test_kcore_hub_decrements_aggregated_per_cta():
-    """k-core on a graph whose hubs (degree > 2^16) take most decrements: the CTA-level
-    aggregation of counted updates to such targets keeps the core exact, for several k, in the
-    graph mode and in the host-loop mode, at the default threshold and with every vertex huge."""
-    g = gg.rmat(17, 16 << 17, 31, symmetrize=True, n_hubs=6, hub_degree=100000)
-    assert int(np.diff(g.offsets.astype(np.int64)).max()) >= 1 << 16
+def test_hub_updates_aggregated_per_cta():
+    """Hubs of degree > 2^16 take most updates (k-core combines its decrements to such targets
+    per CTA in shared memory and applies them once per CTA and round). k-core, sssp, bfs and cc
+    stay exact, for several k and sources, in the graph mode and in the host-loop mode, at the
+    default threshold, with no vertex huge and with every vertex huge."""
+    g = gg.rmat(17, 16 << 17, 31, symmetrize=True, weighted=True, n_hubs=6, hub_degree=100000)
+    deg = np.diff(g.offsets.astype(np.int64))
+    assert int((deg >= 1 << 16).sum()) >= 6
     G = make(g)
     o = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    hub = int(np.argmax(deg))
+    small = int(np.flatnonzero(deg == 3)[0])
+    cc_ref = oracle.cc(g.n, g.offsets, g.indices)
     for params in (dict(), dict(exec_mode=1), dict(hub_threshold=1 << 40), dict(hub_threshold=0)):
         G.set_params(**{"hub_threshold": -1, "exec_mode": 0, **params})
         for k in (2, 16, 40):
             G.kcore(k, o)
             assert np.array_equal(host(o), oracle.kcore(g.n, g.offsets, g.indices, k)), (params, k)
+        for src in (hub, small):
+            G.sssp(src, o)
+            assert np.array_equal(host(o), oracle.sssp(g.n, g.offsets, g.indices, g.weights, src)), (params, src)
+            G.bfs(src, o)
+            assert np.array_equal(host(o), oracle.bfs(g.n, g.offsets, g.indices, src)), (params, src)
+        G.cc(o)
+        assert np.array_equal(host(o), cc_ref), params
+    C = G.clone()
+    C.sssp(hub, o)
+    assert np.array_equal(host(o), oracle.sssp(g.n, g.offsets, g.indices, g.weights, hub))
+    C.close()
     G.close()
