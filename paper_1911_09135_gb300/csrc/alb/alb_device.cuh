@@ -56,6 +56,33 @@ __device__ __forceinline__ uint32_t warp_inclusive_scan(uint32_t x) {
   return x;
 }
 
+// Warp-aggregated append of up to U values per lane (v[u] where pred[u]): a scan of the lanes'
+// counts, one atomicAdd on `count` per warp for all of them, each lane writes its run of slots.
+// Every lane of the warp must call it.
+template <int U>
+__device__ __forceinline__ void warp_append_n(const bool (&pred)[U], const uint32_t (&v)[U], uint32_t* buf,
+                                              uint32_t* count, uint32_t cap = 0xFFFFFFFFu,
+                                              uint32_t* chk = nullptr) {
+  uint32_t cnt = 0u;
+#pragma unroll
+  for (int u = 0; u < U; ++u) cnt += pred[u] ? 1u : 0u;
+  const uint32_t incl = warp_inclusive_scan(cnt);
+  const uint32_t total = __shfl_sync(kFull, incl, 31);
+  if (total == 0u) return;
+  uint32_t base = 0u;
+  if (lane_id() == 0u) base = atomicAdd(count, total);
+  uint32_t slot = __shfl_sync(kFull, base, 0) + incl - cnt;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (pred[u]) {
+      if (ALB_IN_RANGE(chk, 4u, slot, cap)) buf[slot] = v[u];
+      ++slot;
+    }
+  }
+  (void)cap;
+  (void)chk;
+}
+
 // Exclusive scan over the CTA; *total receives the CTA sum. Uses s_warp[kWarps]
 // and synchronises the CTA (every thread must call it).
 template <int BLOCK>

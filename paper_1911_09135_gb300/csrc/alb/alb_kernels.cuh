@@ -44,7 +44,35 @@ struct BfsOp {
   __device__ static bool commit(const OpArgs& a, uint32_t, uint32_t dst, uint32_t) {
     return atomicCAS(a.lab + dst, kInf, a.next) == kInf;
   }
+  // U edges at once: the U CAS are issued before any result is used
+  template <int U>
+  __device__ static void commit_u(const OpArgs& a, const uint32_t (&)[U], const uint32_t (&dst)[U],
+                                  const uint32_t (&)[U], const bool (&w)[U], bool (&push)[U]) {
+    uint32_t old[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) old[u] = w[u] ? atomicCAS(a.lab + dst[u], kInf, a.next) : 0u;
+#pragma unroll
+    for (int u = 0; u < U; ++u) push[u] = w[u] && old[u] == kInf;
+  }
 };
+
+// The min operators' U-edge commit: U non-returning atomicMin, then U stamp reads, then the
+// atomicMax of the stamps that are not yet this round's, then the push decisions; each group of
+// memory operations is issued before any of its results is used.
+template <int U, class Cand>
+__device__ __forceinline__ void min_commit_u(const OpArgs& a, const uint32_t (&dst)[U], const bool (&w)[U],
+                                             bool (&push)[U], Cand cand) {
+#pragma unroll
+  for (int u = 0; u < U; ++u) if (w[u]) atomicMin(a.lab + dst[u], cand(u));
+  uint32_t st[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) st[u] = w[u] ? a.stamp[dst[u]] : a.next;
+  uint32_t old[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) old[u] = st[u] != a.next ? atomicMax(a.stamp + dst[u], a.next) : a.next;
+#pragma unroll
+  for (int u = 0; u < U; ++u) push[u] = old[u] < a.next;
+}
 
 // sssp (push relaxation, Fig. 3): dist[dst] = min(dist[dst], dist[src] + w).
 // The atomicMin does not wait for its old value: a destination whose pre-checked distance
@@ -61,6 +89,11 @@ struct SsspOp {
     atomicMin(a.lab + dst, sv + w);
     return a.stamp[dst] != a.next && atomicMax(a.stamp + dst, a.next) < a.next;
   }
+  template <int U>
+  __device__ static void commit_u(const OpArgs& a, const uint32_t (&sv)[U], const uint32_t (&dst)[U],
+                                  const uint32_t (&wt)[U], const bool (&w)[U], bool (&push)[U]) {
+    min_commit_u<U>(a, dst, w, push, [&](int u) { return sv[u] + wt[u]; });
+  }
 };
 
 // cc (push min-label propagation): label[dst] = min(label[dst], label[src]); the same
@@ -73,6 +106,11 @@ struct CcOp {
   __device__ static bool commit(const OpArgs& a, uint32_t sv, uint32_t dst, uint32_t) {
     atomicMin(a.lab + dst, sv);
     return a.stamp[dst] != a.next && atomicMax(a.stamp + dst, a.next) < a.next;
+  }
+  template <int U>
+  __device__ static void commit_u(const OpArgs& a, const uint32_t (&sv)[U], const uint32_t (&dst)[U],
+                                  const uint32_t (&)[U], const bool (&w)[U], bool (&push)[U]) {
+    min_commit_u<U>(a, dst, w, push, [&](int u) { return sv[u]; });
   }
 };
 
@@ -159,30 +197,31 @@ __device__ __forceinline__ void relax(const TravCtx& c, const OpArgs& a, const u
 #pragma unroll
     for (int u = 0; u < U; ++u) cur[u] = ok[u] ? a.lab[dst[u]] : 0u;
     const uint32_t lane = lane_id();
+    bool push[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const bool w = ok[u] && Op::want(a, sv[u], cur[u], wt[u]);
       const unsigned wm = __ballot_sync(kFull, w);
-      bool push = false;
+      push[u] = false;
       if (w) {
         const unsigned grp = __match_any_sync(wm, dst[u]);
         if ((int)lane == __ffs(grp) - 1) {
           const uint32_t cnt = (uint32_t)__popc(grp);
           if (!(hot_key && cur[u] >= kHotDeg && hot_add(hot_key, hot_cnt, dst[u], cnt)))
-            push = Op::commit_n(a, dst[u], cnt);
+            push[u] = Op::commit_n(a, dst[u], cnt);
         }
       }
-      warp_append(push, dst[u], Fn, ncount, c.n, c.chk);
     }
+    warp_append_n<U>(push, dst, Fn, ncount, c.n, c.chk);
   } else {
     uint32_t cur[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) cur[u] = ok[u] ? a.lab[dst[u]] : 0u;
+    bool w[U], push[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const bool push = ok[u] && Op::want(a, sv[u], cur[u], wt[u]) && Op::commit(a, sv[u], dst[u], wt[u]);
-      warp_append(push, dst[u], Fn, ncount, c.n, c.chk);
-    }
+    for (int u = 0; u < U; ++u) w[u] = ok[u] && Op::want(a, sv[u], cur[u], wt[u]);
+    Op::template commit_u<U>(a, sv, dst, wt, w, push);
+    warp_append_n<U>(push, dst, Fn, ncount, c.n, c.chk);
   }
 }
 
