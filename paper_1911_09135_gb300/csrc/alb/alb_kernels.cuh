@@ -284,6 +284,12 @@ static __device__ __forceinline__ void hub_append(bool huge, uint32_t v, uint32_
 
 // ----------------------------------------------------- inspection + TWC kernel
 
+// Edges relaxed per thread per step (memory requests a thread keeps in flight), per bin.
+constexpr int kUCta = 8;     // CTA bin
+constexpr int kUWarp = 8;    // warp bin
+constexpr int kUThread = 4;  // thread bin (fine-grained gather)
+constexpr int kULb = 8;      // LB kernel
+
 template <class Op>
 __global__ void __launch_bounds__(kBlock) k_inspect(TravCtx c) {
   __shared__ uint32_t s_cb[kBlock], s_cd[kBlock], s_cv[kBlock];       // CTA bin
@@ -314,6 +320,11 @@ __global__ void __launch_bounds__(kBlock) k_inspect(TravCtx c) {
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   unsigned long long twc_edges = 0ull;
 
+  // Tiles of kBlock frontier entries, taken dynamically. Tile t is made of the 32-entry chunks
+  // t, t + T, ..., t + 7T (T tiles; warp w reads chunk t + wT, coalesced): vertices found
+  // together (often of similar degree) spread over many tiles, so no tile holds a run of
+  // CTA-bin vertices that would leave its CTA the last one running.
+  const uint32_t ntiles = (uint32_t)(((uint64_t)nf + kBlock - 1) / kBlock);
   for (;;) {
     if (tid == 0) {
       s_tile = atomicAdd(&st->tile_next, 1u);
@@ -321,10 +332,10 @@ __global__ void __launch_bounds__(kBlock) k_inspect(TravCtx c) {
       s_nwrp = 0u;
     }
     __syncthreads();
-    const uint64_t base = (uint64_t)s_tile * kBlock;
-    if (base >= nf) break;  // CTA-uniform
-    const uint32_t i = (uint32_t)base + tid;
-    bool valid = i < nf;
+    if (s_tile >= ntiles) break;  // CTA-uniform
+    const uint64_t i64 = ((uint64_t)s_tile + (uint64_t)warp * ntiles) * 32u + lane;
+    const uint32_t i = (uint32_t)i64;
+    bool valid = i64 < nf;
     uint32_t v = 0u, beg = 0u, deg = 0u, sv = 0u;
     if (valid) v = all ? i : F[i];
     if (valid && !ALB_IN_RANGE(c.chk, CHK_FRONTIER, v, c.n)) valid = false;
@@ -359,41 +370,41 @@ __global__ void __launch_bounds__(kBlock) k_inspect(TravCtx c) {
     const uint32_t ncta = s_ncta;
     for (uint32_t j = 0; j < ncta; ++j) {
       const uint32_t b = s_cb[j], d = s_cd[j], svj = s_cv[j];
-      for (uint32_t e0 = 0; e0 < d; e0 += kBlock * 4) {
-        uint32_t e[4], s4[4];
-        bool ok[4];
+      for (uint32_t e0 = 0; e0 < d; e0 += kBlock * kUCta) {
+        uint32_t e[kUCta], s4[kUCta];
+        bool ok[kUCta];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kUCta; ++u) {
           const uint32_t q = e0 + u * kBlock + tid;
           ok[u] = q < d; e[u] = b + q; s4[u] = svj;
         }
-        relax<Op, 4>(c, a, e, ok, s4, Fn, ncount, hk, hc);
+        relax<Op, kUCta>(c, a, e, ok, s4, Fn, ncount, hk, hc);
       }
     }
     // Warp bin: one warp per vertex.
     const uint32_t nw = s_nwrp;
     for (uint32_t j = warp; j < nw; j += kWarps) {
       const uint32_t b = s_wb[j], d = s_wd[j], svj = s_wv[j];
-      for (uint32_t e0 = 0; e0 < d; e0 += 32 * 4) {
-        uint32_t e[4], s4[4];
-        bool ok[4];
+      for (uint32_t e0 = 0; e0 < d; e0 += 32 * kUWarp) {
+        uint32_t e[kUWarp], s4[kUWarp];
+        bool ok[kUWarp];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kUWarp; ++u) {
           const uint32_t q = e0 + u * 32 + lane;
           ok[u] = q < d; e[u] = b + q; s4[u] = svj;
         }
-        relax<Op, 4>(c, a, e, ok, s4, Fn, ncount, hk, hc);
+        relax<Op, kUWarp>(c, a, e, ok, s4, Fn, ncount, hk, hc);
       }
     }
     // Thread bin: the small vertices' edges, gathered over the whole CTA
     // (consecutive threads take consecutive edges of the concatenated lists).
     const uint32_t S = s_scan[kBlock];
     uint32_t owner = 0u;
-    for (uint32_t q0 = 0; q0 < S; q0 += kBlock * 2) {
-      uint32_t e[2], s2[2];
-      bool ok[2];
+    for (uint32_t q0 = 0; q0 < S; q0 += kBlock * kUThread) {
+      uint32_t e[kUThread], s2[kUThread];
+      bool ok[kUThread];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < kUThread; ++u) {
         const uint32_t q = q0 + u * kBlock + tid;
         ok[u] = q < S;
         e[u] = 0u; s2[u] = 0u;
@@ -403,7 +414,7 @@ __global__ void __launch_bounds__(kBlock) k_inspect(TravCtx c) {
           s2[u] = s_sv[owner];
         }
       }
-      relax<Op, 2>(c, a, e, ok, s2, Fn, ncount, hk, hc);
+      relax<Op, kUThread>(c, a, e, ok, s2, Fn, ncount, hk, hc);
     }
     __syncthreads();
   }
@@ -501,7 +512,7 @@ __global__ void __launch_bounds__(kBlock) k_lb(TravCtx c) {
 
   const uint64_t p = (uint64_t)gridDim.x * kBlock;
   const uint64_t gt = (uint64_t)blockIdx.x * kBlock + tid;
-  constexpr int U = 4;
+  constexpr int U = kULb;
   unsigned long long lb_edges = 0ull;  // positions this thread processed (cta_stats)
   auto process = [&](const uint64_t (&k)[U], const bool (&ok)[U]) {
     uint32_t ed[U], sv[U], src[U];
