@@ -47,6 +47,7 @@ KERNEL_NAMES = {
     ("pr", "twc"): "k_pr_pull", ("pr", "lb"): "k_pr_hub",
 }
 KERNEL_SOURCES = ["paper_1911_09135_gb300/csrc/alb/alb_traverse.cu",
+                  "paper_1911_09135_gb300/csrc/alb/alb_kernels.cuh",
                   "paper_1911_09135_gb300/csrc/alb/alb_pagerank.cu",
                   "paper_1911_09135_gb300/csrc/alb/alb_device.cuh",
                   "paper_1911_09135_gb300/csrc/alb/alb_internal.cuh"]

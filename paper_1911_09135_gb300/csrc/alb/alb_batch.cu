@@ -191,10 +191,11 @@ __global__ void __launch_bounds__(kBlock) k_batch_out(TravCtx c) {
 template <int APP>
 __global__ void __launch_bounds__(kBlock) k_multi_init(TravCtx c) {
   uint32_t* lab = c.args->lab;
-  for (uint64_t v = (uint64_t)blockIdx.x * kBlock + threadIdx.x; v < c.n; v += (uint64_t)gridDim.x * kBlock) {
+  for (uint64_t v = (uint64_t)blockIdx.x * kBlock + threadIdx.x; v < c.n; v += (uint64_t)gridDim.x * kBlock)
     lab[v] = kInf;
-    if (APP == APP_SSSP) c.stamp[v] = 0u;
-  }
+  if (APP == APP_SSSP && c.pushed)
+    for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < 2ull * c.pw; i += (uint64_t)gridDim.x * kBlock)
+      c.pushed[i] = 0u;
 }
 
 __global__ void k_multi_seed(TravCtx c) {

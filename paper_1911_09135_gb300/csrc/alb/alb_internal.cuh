@@ -71,7 +71,9 @@ struct TravCtx {
   uint32_t* F1;
   uint32_t* hub_v;        // huge worklist "work"
   uint32_t* hub_p;        // exclusive prefix sum of huge degrees ("prefixWork")
-  uint32_t* stamp;        // round stamps: dedup of next-frontier pushes (sssp, cc)
+  uint32_t* pushed;       // two bitmaps of pw words; bitmap r & 1 marks the vertices pushed in
+                          // round r (dedup of next-frontier pushes, sssp and cc)
+  uint32_t pw;            // words per bitmap: ceil(n / 32)
   RoundState* st;
   const CallArgs* args;
   cudaGraphConditionalHandle h_while;
@@ -128,7 +130,7 @@ struct alb_graph_s {
   uint32_t* F1 = nullptr;
   uint32_t* hub_v = nullptr;
   uint32_t* hub_p = nullptr;
-  uint32_t* stamp = nullptr;
+  uint32_t* pushed = nullptr;       // 2 x ceil(n / 32) words (TravCtx::pushed)
   uint32_t* tmp = nullptr;        // n-entry scratch output when the caller's buffer is host memory
   alb::RoundState* st = nullptr;
   alb::CallArgs* args = nullptr;

@@ -27,8 +27,8 @@ namespace alb {
 
 struct OpArgs {
   uint32_t* lab;
-  uint32_t* stamp;
-  uint32_t next;  // round + 1
+  uint32_t* pushed;  // this round's push bitmap (sssp, cc)
+  uint32_t next;     // round + 1
   uint32_t k;
   const void* aux;  // operator-specific state (the multi-source operators)
   uint32_t n;
@@ -56,38 +56,52 @@ struct BfsOp {
   }
 };
 
-// The min operators' U-edge commit: U non-returning atomicMin, then U stamp reads, then the
-// atomicMax of the stamps that are not yet this round's, then the push decisions; each group of
-// memory operations is issued before any of its results is used.
+// Push of a min operator's destination, at most once per round: the first thread to set the
+// vertex's bit in this round's bitmap pushes it (a plain read of the word skips the atomic when
+// the bit is already set). The bitmaps are 1/32 the size of a per-vertex round stamp, so they and
+// the labels stay in L2 together.
+__device__ __forceinline__ bool claim_push(const OpArgs& a, uint32_t dst) {
+  const uint32_t bit = 1u << (dst & 31u);
+  uint32_t* word = a.pushed + (dst >> 5);
+  return !(*word & bit) && !(atomicOr(word, bit) & bit);
+}
+
+// The min operators' U-edge commit: U non-returning atomicMin, then U bitmap reads, then the
+// atomicOr of the bits not yet set, then the push decisions; each group of memory operations is
+// issued before any of its results is used.
 template <int U, class Cand>
 __device__ __forceinline__ void min_commit_u(const OpArgs& a, const uint32_t (&dst)[U], const bool (&w)[U],
                                              bool (&push)[U], Cand cand) {
 #pragma unroll
   for (int u = 0; u < U; ++u) if (w[u]) atomicMin(a.lab + dst[u], cand(u));
-  uint32_t st[U];
+  uint32_t wd[U];
 #pragma unroll
-  for (int u = 0; u < U; ++u) st[u] = w[u] ? a.stamp[dst[u]] : a.next;
+  for (int u = 0; u < U; ++u) wd[u] = w[u] ? a.pushed[dst[u] >> 5] : 0xFFFFFFFFu;
   uint32_t old[U];
 #pragma unroll
-  for (int u = 0; u < U; ++u) old[u] = st[u] != a.next ? atomicMax(a.stamp + dst[u], a.next) : a.next;
+  for (int u = 0; u < U; ++u) {
+    const uint32_t bit = 1u << (dst[u] & 31u);
+    old[u] = (wd[u] & bit) ? bit : atomicOr(a.pushed + (dst[u] >> 5), bit);
+  }
 #pragma unroll
-  for (int u = 0; u < U; ++u) push[u] = old[u] < a.next;
+  for (int u = 0; u < U; ++u) push[u] = w[u] && !(old[u] & (1u << (dst[u] & 31u)));
 }
 
 // sssp (push relaxation, Fig. 3): dist[dst] = min(dist[dst], dist[src] + w).
 // The atomicMin does not wait for its old value: a destination whose pre-checked distance
-// improves is pushed (once per round, by its round stamp), so every vertex whose distance drops
-// is in the next frontier.
+// improves is pushed (once per round, by its bit in the round's push bitmap), so every vertex
+// whose distance drops is in the next frontier.
 struct SsspOp {
   static constexpr bool kBatch = false;
   static constexpr bool kW = true;
+  static constexpr bool kPushBitmap = true;
   __device__ static uint32_t sval(const OpArgs& a, uint32_t u) { return a.lab[u]; }
   __device__ static bool want(const OpArgs&, uint32_t sv, uint32_t cur, uint32_t w) {
     return (uint64_t)sv + w < (uint64_t)cur;
   }
   __device__ static bool commit(const OpArgs& a, uint32_t sv, uint32_t dst, uint32_t w) {
     atomicMin(a.lab + dst, sv + w);
-    return a.stamp[dst] != a.next && atomicMax(a.stamp + dst, a.next) < a.next;
+    return claim_push(a, dst);
   }
   template <int U>
   __device__ static void commit_u(const OpArgs& a, const uint32_t (&sv)[U], const uint32_t (&dst)[U],
@@ -97,15 +111,16 @@ struct SsspOp {
 };
 
 // cc (push min-label propagation): label[dst] = min(label[dst], label[src]); the same
-// non-blocking update and round-stamp push as sssp.
+// non-blocking update and once-per-round push as sssp.
 struct CcOp {
   static constexpr bool kBatch = false;
   static constexpr bool kW = false;
+  static constexpr bool kPushBitmap = true;
   __device__ static uint32_t sval(const OpArgs& a, uint32_t u) { return a.lab[u]; }
   __device__ static bool want(const OpArgs&, uint32_t sv, uint32_t cur, uint32_t) { return sv < cur; }
   __device__ static bool commit(const OpArgs& a, uint32_t sv, uint32_t dst, uint32_t) {
     atomicMin(a.lab + dst, sv);
-    return a.stamp[dst] != a.next && atomicMax(a.stamp + dst, a.next) < a.next;
+    return claim_push(a, dst);
   }
   template <int U>
   __device__ static void commit_u(const OpArgs& a, const uint32_t (&sv)[U], const uint32_t (&dst)[U],
@@ -132,6 +147,11 @@ struct KcoreOp {
   }
   __device__ static bool commit(const OpArgs& a, uint32_t, uint32_t dst, uint32_t) { return commit_n(a, dst, 1u); }
 };
+
+template <class Op, class = void>
+struct uses_push_bitmap { static constexpr bool value = false; };
+template <class Op>
+struct uses_push_bitmap<Op, decltype(void(Op::kPushBitmap))> { static constexpr bool value = Op::kPushBitmap; };
 
 template <class Op, class = void>
 struct aggregates { static constexpr bool value = false; };
@@ -316,9 +336,16 @@ __global__ void __launch_bounds__(kBlock) k_inspect(TravCtx c) {
   uint32_t* Fn = cur ? c.F0 : c.F1;
   uint32_t* ncount = &st->fcount[cur ^ 1u];
   const CallArgs* ca = c.args;
-  const OpArgs a{ca->lab, c.stamp, r + 1u, ca->k, ca->aux, c.n, c.chk};
+  const OpArgs a{ca->lab, c.pushed ? c.pushed + (size_t)cur * c.pw : nullptr, r + 1u, ca->k, ca->aux, c.n, c.chk};
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   unsigned long long twc_edges = 0ull;
+  if constexpr (uses_push_bitmap<Op>::value) {
+    // the other bitmap (last round's) is cleared for the next round
+    if (c.pushed) {
+      uint32_t* other = c.pushed + (size_t)(cur ^ 1u) * c.pw;
+      for (uint32_t i = blockIdx.x * kBlock + tid; i < c.pw; i += gridDim.x * kBlock) other[i] = 0u;
+    }
+  }
 
   // Tiles of kBlock frontier entries, taken dynamically. Tile t is made of the 32-entry chunks
   // t, t + T, ..., t + 7T (T tiles; warp w reads chunk t + wT, coalesced): vertices found
@@ -470,7 +497,7 @@ __global__ void __launch_bounds__(kBlock) k_lb(TravCtx c) {
   uint32_t* Fn = cur ? c.F0 : c.F1;
   uint32_t* ncount = &st->fcount[cur ^ 1u];
   const CallArgs* ca = c.args;
-  const OpArgs a{ca->lab, c.stamp, r + 1u, ca->k, ca->aux, c.n, c.chk};
+  const OpArgs a{ca->lab, c.pushed ? c.pushed + (size_t)cur * c.pw : nullptr, r + 1u, ca->k, ca->aux, c.n, c.chk};
   const uint32_t tid = threadIdx.x, lane = tid & 31u;
 
   const bool staged = nh <= (uint32_t)kStage;
@@ -585,14 +612,18 @@ __global__ void __launch_bounds__(kBlock) k_init(TravCtx c) {
     if constexpr (APP == APP_BFS) {
       if (ok) lab[v] = (v == src) ? 0u : kInf;
     } else if constexpr (APP == APP_SSSP) {
-      if (ok) { lab[v] = (v == src) ? 0u : kInf; c.stamp[v] = 0u; }
+      if (ok) lab[v] = (v == src) ? 0u : kInf;
     } else if constexpr (APP == APP_CC) {
-      if (ok) { lab[v] = v; c.stamp[v] = 0u; }
+      if (ok) lab[v] = v;
     } else if constexpr (APP == APP_KCORE) {
       uint32_t d = 0u;
       if (ok) { d = c.off[v + 1] - c.off[v]; lab[v] = d; }
       warp_append(ok && d < k, v, c.F0, &st->fcount[0], c.n, c.chk);
     }
+  }
+  if constexpr (APP == APP_SSSP || APP == APP_CC) {  // both push bitmaps start empty
+    for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < 2ull * c.pw; i += (uint64_t)gridDim.x * kBlock)
+      c.pushed[i] = 0u;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if constexpr (APP == APP_BFS || APP == APP_SSSP) { c.F0[0] = src; st->fcount[0] = 1u; }

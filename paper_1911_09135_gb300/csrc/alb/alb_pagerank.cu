@@ -139,18 +139,24 @@ __global__ void __launch_bounds__(kBlock) k_pr_count(const uint32_t* off, uint32
   if (threadIdx.x < 5) cnt[blockIdx.x * 5 + threadIdx.x] = s[threadIdx.x];
 }
 
-// Exclusive scan of the per-block counts of each bin (one CTA, serial over blocks per bin).
-__global__ void k_pr_scan_counts(uint32_t* cnt, uint32_t nblk, uint32_t* totals) {
-  if (threadIdx.x < 5) {
-    const uint32_t b = threadIdx.x;
-    uint32_t run = 0;
-    for (uint32_t i = 0; i < nblk; ++i) {
-      const uint32_t c = cnt[i * 5 + b];
-      cnt[i * 5 + b] = run;
-      run += c;
-    }
-    totals[b] = run;
+// Exclusive scan of the per-block counts of each bin: CTA b scans bin b (carried CTA scans).
+__global__ void __launch_bounds__(kBlock) k_pr_scan_counts(uint32_t* cnt, uint32_t nblk, uint32_t* totals) {
+  __shared__ uint32_t s_warp[kWarps + 1];
+  __shared__ uint32_t s_carry;
+  const uint32_t b = blockIdx.x;
+  if (threadIdx.x == 0) s_carry = 0u;
+  __syncthreads();
+  for (uint32_t i0 = 0; i0 < nblk; i0 += kBlock) {
+    const uint32_t i = i0 + threadIdx.x;
+    const uint32_t c = i < nblk ? cnt[i * 5 + b] : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_exclusive_scan<kBlock>(c, s_warp, &tot);
+    if (i < nblk) cnt[i * 5 + b] = s_carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry += tot;
+    __syncthreads();
   }
+  if (threadIdx.x == 0) totals[b] = s_carry;
 }
 
 __global__ void __launch_bounds__(kBlock) k_pr_scatter(const uint32_t* off, uint32_t n, uint32_t t,
@@ -720,7 +726,7 @@ static alb_status pr_setup(alb_graph g, cudaStream_t s) {
   const uint32_t t = g->threshold, wmin = g->params.twc_warp_min, cmin = g->params.twc_cta_min;
   uint32_t* totals = w->cnt + 5 * (size_t)nblk;
   k_pr_count<<<nblk, kBlock, 0, s>>>(g->off, n, t, wmin, cmin, w->cnt);
-  k_pr_scan_counts<<<1, 32, 0, s>>>(w->cnt, nblk, totals);
+  k_pr_scan_counts<<<5, kBlock, 0, s>>>(w->cnt, nblk, totals);
   uint32_t h[5];
   ALB_CUDA_TRY(cudaMemcpyAsync(h, totals, sizeof(h), cudaMemcpyDeviceToHost, s));
   ALB_CUDA_TRY(cudaStreamSynchronize(s));

@@ -113,7 +113,8 @@ TravCtx make_ctx(alb_graph g, bool use_graph, cudaGraphConditionalHandle hw,
   c.F1 = g->F1;
   c.hub_v = g->hub_v;
   c.hub_p = g->hub_p;
-  c.stamp = g->stamp;
+  c.pushed = g->pushed;
+  c.pw = (uint32_t)(((size_t)g->n + 31) / 32);
   c.st = g->st;
   c.args = g->args;
   c.h_while = hw;
@@ -473,7 +474,8 @@ extern "C" alb_status alb_bfs_noalloc(uint32_t n, uint64_t m, const uint32_t* d_
   c.F1 = F1;
   c.hub_v = hub_v;
   c.hub_p = hub_p;
-  c.stamp = nullptr;  // bfs needs no round stamps
+  c.pushed = nullptr;  // bfs needs no push bitmaps
+  c.pw = 0u;
   c.st = st;
   c.args = args;
 
