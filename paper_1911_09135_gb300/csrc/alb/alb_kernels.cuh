@@ -207,11 +207,10 @@ __device__ __forceinline__ void relax(const TravCtx& c, const OpArgs& a, const u
   for (int u = 0; u < U; ++u) wt[u] = (Op::kW && ok[u]) ? __ldcs(c.w + e[u]) : 0u;
   if constexpr (Op::kBatch) {
     // multi-source operators do their own label reads (a row of sources per vertex)
+    bool push[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const bool push = ok[u] && Op::apply(a, sv[u], dst[u], wt[u]);
-      warp_append(push, dst[u], Fn, ncount, c.n, c.chk);
-    }
+    for (int u = 0; u < U; ++u) push[u] = ok[u] && Op::apply(a, sv[u], dst[u], wt[u]);
+    warp_append_n<U>(push, dst, Fn, ncount, c.n, c.chk);
   } else if constexpr (aggregates<Op>::value) {
     uint32_t cur[U];
 #pragma unroll
