@@ -30,7 +30,7 @@ from . import alb
 
 GROUP = 32
 KINDS = ("bfs", "sssp", "cc")
-EDGES_PER_CTA = 1 << 17       # serving grids: one CTA per this many edges, at most 2 per SM
+EDGES_PER_CTA = 1 << 17       # serving grids: one CTA per this many edges, at most ctas_per_sm per SM
 
 
 @dataclasses.dataclass
@@ -97,7 +97,7 @@ class _Graph:
         multi-source workspace (148 bytes per vertex) and the round workspace (20 per vertex)."""
         return n * (4 * (2 * GROUP + 1) + 148 + 20)
 
-    def __init__(self, torch, csr, tune: bool, slots: int, priority: int):
+    def __init__(self, torch, csr, tune: bool, slots: int, priority: int, ctas_per_sm: int = 2):
         self.n = csr.n
         self.m = csr.m
         self.deg = csr.degrees().astype(np.int64)
@@ -108,7 +108,7 @@ class _Graph:
         # ends: small graphs get a grid sized to their edges, large ones two CTAs per SM, so
         # kernels of several slots share the SMs.
         sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-        G.set_params(grid_blocks=min(2 * sms, max(16, -(-csr.m // EDGES_PER_CTA))))
+        G.set_params(grid_blocks=min(ctas_per_sm * sms, max(16, -(-csr.m // EDGES_PER_CTA))))
         if tune:
             src = int(np.argmax(self.deg))
             for k in KINDS:
@@ -138,7 +138,8 @@ class Server:
     """One slot per resident graph; see the module docstring."""
 
     def __init__(self, graphs, *, tune: bool = True, keep_results: bool = False,
-                 hbm_reserve: int = 1 << 30, big_graph_edges: int = 50_000_000, big_slots: int = 2):
+                 hbm_reserve: int = 1 << 30, big_graph_edges: int = 50_000_000, big_slots: int = 2,
+                 ctas_per_sm: int = 2):
         import torch
         self.torch = torch
         # smaller graphs get higher stream priority, so their short rounds are scheduled
@@ -146,7 +147,7 @@ class Server:
         lo, hi = torch.cuda.Stream.priority_range()
         order = np.argsort(np.argsort([g.m for g in graphs]))
         prio = [hi if order[i] < len(graphs) // 2 else lo for i in range(len(graphs))]
-        self.graphs = [_Graph(torch, g, tune, big_slots if g.m >= big_graph_edges else 1, prio[i])
+        self.graphs = [_Graph(torch, g, tune, big_slots if g.m >= big_graph_edges else 1, prio[i], ctas_per_sm)
                        for i, g in enumerate(graphs)]
         self.keep = keep_results
         self.reserve = hbm_reserve
