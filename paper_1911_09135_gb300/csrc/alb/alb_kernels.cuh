@@ -187,14 +187,81 @@ __device__ __forceinline__ bool hot_add(uint32_t* key, uint32_t* cnt, uint32_t v
   return false;
 }
 
+// Where pushes go: the next frontier (global) and, in the TWC kernel, a CTA staging buffer in
+// shared memory. Every warp of every CTA appends to the same frontier counter, and same-address
+// atomics serialise in L2, so the TWC kernel collects a tile's pushes in shared memory (one
+// shared atomic per warp and step) and moves them to the frontier with one global atomic per
+// tile. Pushes that do not fit in the buffer go to the frontier directly.
+constexpr uint32_t kPushBuf = 2048;
+
+struct PushSink {
+  uint32_t* Fn;      // next frontier
+  uint32_t* ncount;  // its length
+  uint32_t cap;      // its capacity (n)
+  uint32_t* chk;
+  uint32_t* sbuf;    // CTA staging buffer (shared memory), or null: push to Fn directly
+  uint32_t* sn;      // entries claimed in it (may exceed kPushBuf; the excess went to Fn)
+};
+
+// Warp-aggregated push of up to U values per lane (v[u] where pred[u]); every lane of the warp
+// calls it.
+template <int U>
+__device__ __forceinline__ void push_n(const bool (&pred)[U], const uint32_t (&v)[U], const PushSink& k) {
+  if (!k.sbuf) {
+    warp_append_n<U>(pred, v, k.Fn, k.ncount, k.cap, k.chk);
+    return;
+  }
+  uint32_t cnt = 0u;
+#pragma unroll
+  for (int u = 0; u < U; ++u) cnt += pred[u] ? 1u : 0u;
+  const uint32_t incl = warp_inclusive_scan(cnt);
+  const uint32_t total = __shfl_sync(kFull, incl, 31);
+  if (total == 0u) return;
+  uint32_t base = 0u, gbase = 0u;
+  if (lane_id() == 0u) {
+    base = atomicAdd(k.sn, total);
+    const uint32_t end = base + total;
+    if (end > kPushBuf) gbase = atomicAdd(k.ncount, end - (base > kPushBuf ? base : kPushBuf));
+  }
+  base = __shfl_sync(kFull, base, 0);
+  gbase = __shfl_sync(kFull, gbase, 0);
+  const uint32_t over0 = base > kPushBuf ? base : kPushBuf;  // first position sent to Fn
+  uint32_t pos = base + incl - cnt;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (pred[u]) {
+      if (pos < kPushBuf) {
+        k.sbuf[pos] = v[u];
+      } else {
+        const uint32_t g = gbase + (pos - over0);
+        if (ALB_IN_RANGE(k.chk, 4u, g, k.cap)) k.Fn[g] = v[u];
+      }
+      ++pos;
+    }
+  }
+}
+
+// Move the staged pushes to the frontier: one global atomic, coalesced stores. Called by every
+// thread of the CTA after a barrier that follows the tile's last push.
+__device__ __forceinline__ void push_flush(const PushSink& k, uint32_t* s_base) {
+  const uint32_t nb = *k.sn < kPushBuf ? *k.sn : kPushBuf;
+  if (nb == 0u) return;  // CTA-uniform
+  if (threadIdx.x == 0) *s_base = atomicAdd(k.ncount, nb);
+  __syncthreads();
+  const uint32_t b = *s_base;
+  for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) {
+    const uint32_t g = b + j;
+    if (ALB_IN_RANGE(k.chk, 4u, g, k.cap)) k.Fn[g] = k.sbuf[j];
+  }
+}
+
 // Relax U edges per thread; all loads are issued before the atomics so each
 // thread keeps U independent memory requests in flight. Warp-uniform callers.
 // hot_key / hot_cnt: the CTA's aggregation table (counted operators; null = none).
 template <class Op, int U>
 __device__ __forceinline__ void relax(const TravCtx& c, const OpArgs& a, const uint32_t (&e)[U],
-                                      const bool (&ok_in)[U], const uint32_t (&sv)[U], uint32_t* Fn,
-                                      uint32_t* ncount, uint32_t* hot_key = nullptr,
-                                      uint32_t* hot_cnt = nullptr) {
+                                      const bool (&ok_in)[U], const uint32_t (&sv)[U], const PushSink& sink,
+                                      uint32_t* hot_key = nullptr, uint32_t* hot_cnt = nullptr) {
   uint32_t dst[U], wt[U];
   bool ok[U];
 #pragma unroll
@@ -210,7 +277,7 @@ __device__ __forceinline__ void relax(const TravCtx& c, const OpArgs& a, const u
     bool push[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) push[u] = ok[u] && Op::apply(a, sv[u], dst[u], wt[u]);
-    warp_append_n<U>(push, dst, Fn, ncount, c.n, c.chk);
+    push_n<U>(push, dst, sink);
   } else if constexpr (aggregates<Op>::value) {
     uint32_t cur[U];
 #pragma unroll
@@ -231,7 +298,7 @@ __device__ __forceinline__ void relax(const TravCtx& c, const OpArgs& a, const u
         }
       }
     }
-    warp_append_n<U>(push, dst, Fn, ncount, c.n, c.chk);
+    push_n<U>(push, dst, sink);
   } else {
     uint32_t cur[U];
 #pragma unroll
@@ -240,7 +307,7 @@ __device__ __forceinline__ void relax(const TravCtx& c, const OpArgs& a, const u
 #pragma unroll
     for (int u = 0; u < U; ++u) w[u] = ok[u] && Op::want(a, sv[u], cur[u], wt[u]);
     Op::template commit_u<U>(a, sv, dst, wt, w, push);
-    warp_append_n<U>(push, dst, Fn, ncount, c.n, c.chk);
+    push_n<U>(push, dst, sink);
   }
 }
 
@@ -316,6 +383,8 @@ __global__ void __launch_bounds__(kBlock) k_inspect(TravCtx c) {
   __shared__ uint32_t s_scan[kBlock + 1], s_sb[kBlock], s_sv[kBlock];  // thread bin
   __shared__ uint32_t s_warp[kWarps + 1];
   __shared__ uint32_t s_ncta, s_nwrp, s_tile;
+  __shared__ uint32_t s_push[kPushBuf];  // the tile's pushes (PushSink)
+  __shared__ uint32_t s_npush, s_pbase;
   constexpr bool kHot = aggregates<Op>::value;
   constexpr uint32_t kHotN = kHot ? kHotSlots : 1u;
   __shared__ uint32_t s_hkey[kHotN], s_hcnt[kHotN];  // counted operators: CTA aggregation table
@@ -338,6 +407,7 @@ __global__ void __launch_bounds__(kBlock) k_inspect(TravCtx c) {
   const OpArgs a{ca->lab, c.pushed ? c.pushed + (size_t)cur * c.pw : nullptr, r + 1u, ca->k, ca->aux, c.n, c.chk};
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   unsigned long long twc_edges = 0ull;
+  const PushSink sink{Fn, ncount, c.n, c.chk, s_push, &s_npush};
   if constexpr (uses_push_bitmap<Op>::value) {
     // the other bitmap (last round's) is cleared for the next round
     if (c.pushed) {
@@ -356,6 +426,7 @@ __global__ void __launch_bounds__(kBlock) k_inspect(TravCtx c) {
       s_tile = atomicAdd(&st->tile_next, 1u);
       s_ncta = 0u;
       s_nwrp = 0u;
+      s_npush = 0u;
     }
     __syncthreads();
     if (s_tile >= ntiles) break;  // CTA-uniform
@@ -404,7 +475,7 @@ __global__ void __launch_bounds__(kBlock) k_inspect(TravCtx c) {
           const uint32_t q = e0 + u * kBlock + tid;
           ok[u] = q < d; e[u] = b + q; s4[u] = svj;
         }
-        relax<Op, kUCta>(c, a, e, ok, s4, Fn, ncount, hk, hc);
+        relax<Op, kUCta>(c, a, e, ok, s4, sink, hk, hc);
       }
     }
     // Warp bin: one warp per vertex.
@@ -419,7 +490,7 @@ __global__ void __launch_bounds__(kBlock) k_inspect(TravCtx c) {
           const uint32_t q = e0 + u * 32 + lane;
           ok[u] = q < d; e[u] = b + q; s4[u] = svj;
         }
-        relax<Op, kUWarp>(c, a, e, ok, s4, Fn, ncount, hk, hc);
+        relax<Op, kUWarp>(c, a, e, ok, s4, sink, hk, hc);
       }
     }
     // Thread bin: the small vertices' edges, gathered over the whole CTA
@@ -440,9 +511,10 @@ __global__ void __launch_bounds__(kBlock) k_inspect(TravCtx c) {
           s2[u] = s_sv[owner];
         }
       }
-      relax<Op, kUThread>(c, a, e, ok, s2, Fn, ncount, hk, hc);
+      relax<Op, kUThread>(c, a, e, ok, s2, sink, hk, hc);
     }
     __syncthreads();
+    push_flush(sink, &s_pbase);
   }
   if constexpr (kHot) {
     // apply the CTA's pending counts: one atomic per target; the one that crosses k pushes it
@@ -498,6 +570,7 @@ __global__ void __launch_bounds__(kBlock) k_lb(TravCtx c) {
   const CallArgs* ca = c.args;
   const OpArgs a{ca->lab, c.pushed ? c.pushed + (size_t)cur * c.pw : nullptr, r + 1u, ca->k, ca->aux, c.n, c.chk};
   const uint32_t tid = threadIdx.x, lane = tid & 31u;
+  const PushSink sink{Fn, ncount, c.n, c.chk, nullptr, nullptr};
 
   const bool staged = nh <= (uint32_t)kStage;
   if (staged) {
@@ -560,7 +633,7 @@ __global__ void __launch_bounds__(kBlock) k_lb(TravCtx c) {
         }
       }
     } else {
-      relax<Op, U>(c, a, ed, ok, sv, Fn, ncount);
+      relax<Op, U>(c, a, ed, ok, sv, sink);
     }
   };
 
