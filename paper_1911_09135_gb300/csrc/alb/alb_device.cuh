@@ -130,4 +130,16 @@ __device__ __forceinline__ uint32_t upper_search(const uint32_t* P, uint32_t lo,
   return lo;
 }
 
+// upper_search for a caller whose k only grows (the LB kernels' positions): the next position
+// usually falls in the same entry or the next one, so two linear steps are tried before the
+// binary search.
+__device__ __forceinline__ uint32_t advance_search(const uint32_t* P, uint32_t lo, uint32_t hi, uint32_t k) {
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    if (lo + 1 >= hi || P[lo + 1] > k) return lo;
+    ++lo;
+  }
+  return upper_search(P, lo, hi, k);
+}
+
 }  // namespace alb

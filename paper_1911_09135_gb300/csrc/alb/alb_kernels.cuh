@@ -590,7 +590,7 @@ __global__ void __launch_bounds__(kBlock) k_lb(TravCtx c) {
   // source lookup for position k; j only grows along a thread's positions
   uint32_t j = 0u, jc = kInf, base_c = 0u, val_c = 0u, src_c = 0u;
   auto resolve = [&](uint32_t k, uint32_t& edge, uint32_t& sv, uint32_t& src) {
-    j = upper_search(P, j, nh, k);
+    j = advance_search(P, j, nh, k);
     if (!ALB_IN_RANGE(c.chk, CHK_SRC, j, nh)) j = 0u;
     if (staged) {
       edge = k + s_base[j];

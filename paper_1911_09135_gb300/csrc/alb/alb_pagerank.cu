@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(kBlock) k_pr_hub(PrCtx c) {
       jj[u] = kInf;
       id[u] = kInf;
       if (k < e) {
-        j = upper_search(P, j, nh, (uint32_t)k);
+        j = advance_search(P, j, nh, (uint32_t)k);
         jj[u] = j;
         const uint32_t base = staged ? s_base[j] : c.off[c.hubs[j]] - c.hub_p[j];
         id[u] = __ldcs(c.idx + (uint32_t)k + base);
@@ -520,6 +520,14 @@ __global__ void __launch_bounds__(kBlock) k_pr_hub(PrCtx c) {
     for (int u = 0; u < U; ++u) val[u] = id[u] != kInf ? __ldg(cb + id[u]) : 0.0f;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
+      const uint32_t slot0 = (uint32_t)((k0 + (uint64_t)u * p) >> 5);
+      const uint32_t j0 = __shfl_sync(kFull, jj[u], 0);
+      if (__all_sync(kFull, jj[u] == j0) && j0 != kInf) {
+        // the usual case: all 32 positions belong to one huge vertex, one sum
+        const float t = warp_sum(val[u]);
+        if (lane == 0) c.part[slot0 + j0] = t;
+        continue;
+      }
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const float y = __shfl_up_sync(kFull, val[u], o);
@@ -528,7 +536,7 @@ __global__ void __launch_bounds__(kBlock) k_pr_hub(PrCtx c) {
       }
       const uint32_t jn = __shfl_down_sync(kFull, jj[u], 1);
       const bool tail = jj[u] != kInf && (lane == 31 || jn != jj[u]);
-      if (tail) c.part[(uint32_t)((k0 + (uint64_t)u * p) >> 5) + jj[u]] = val[u];
+      if (tail) c.part[slot0 + jj[u]] = val[u];
     }
   }
   if (c.cta_lb) {
