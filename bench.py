@@ -387,6 +387,11 @@ def gpu_arm(args, dist):
             roof = {"bound": "hbm", "kernel": top["kernel"], "achieved": round(achieved, 1),
                     "peak": peak, "peak_source": which, "unit": "GB/s",
                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                    # the same launches' measured DRAM bytes (ncu) over their live duration
+                    "dram_gbs": (round(traffic / (top["ms"] / top["launches"] * 1e-3) / 1e9, 1)
+                                 if traffic else None),
+                    "dram_frac": (round(traffic / (top["ms"] / top["launches"] * 1e-3) / 1e9 / peak, 4)
+                                  if traffic else None),
                     "algorithmic_bytes_per_launch": int(top["bytes"] / top["launches"]),
                     "avg_launch_ms": round(top["ms"] / top["launches"], 4),
                     "launches": top["launches"],
