@@ -553,6 +553,8 @@ __global__ void __launch_bounds__(kBlock) k_lb(TravCtx c) {
   __shared__ uint32_t s_base[kStage];
   __shared__ uint32_t s_val[kStage];
   __shared__ uint32_t s_src[kTrace ? kStage : 1];
+  __shared__ uint32_t s_push[kTrace ? 1 : kPushBuf];  // one step's pushes (PushSink)
+  __shared__ uint32_t s_npush, s_pbase;
 
   RoundState* st = c.st;
   const unsigned long long hp = st->hub_packed;
@@ -570,7 +572,10 @@ __global__ void __launch_bounds__(kBlock) k_lb(TravCtx c) {
   const CallArgs* ca = c.args;
   const OpArgs a{ca->lab, c.pushed ? c.pushed + (size_t)cur * c.pw : nullptr, r + 1u, ca->k, ca->aux, c.n, c.chk};
   const uint32_t tid = threadIdx.x, lane = tid & 31u;
-  const PushSink sink{Fn, ncount, c.n, c.chk, nullptr, nullptr};
+  // a step of the CTA is kBlock x U positions, at most one push each: the buffer never overflows
+  static_assert(kTrace || kBlock * kULb <= kPushBuf, "one LB step's pushes must fit the CTA buffer");
+  const PushSink sink{Fn, ncount, c.n, c.chk, kTrace ? nullptr : s_push, &s_npush};
+  if (threadIdx.x == 0) s_npush = 0u;
 
   const bool staged = nh <= (uint32_t)kStage;
   if (staged) {
@@ -637,14 +642,26 @@ __global__ void __launch_bounds__(kBlock) k_lb(TravCtx c) {
     }
   };
 
+  // after each CTA-uniform step: the step's staged pushes go to the frontier in one atomic
+  auto flush = [&]() {
+    if constexpr (!kTrace) {
+      __syncthreads();
+      push_flush(sink, &s_pbase);
+      if (threadIdx.x == 0) s_npush = 0u;  // every thread read the count inside push_flush
+      __syncthreads();
+    }
+  };
   if (c.distribution == 0u) {
     // cyclic: thread gt takes positions gt, gt + p, gt + 2p, ... (Sec. 4.1)
-    for (uint64_t k0 = gt - lane; k0 < e; k0 += p * U) {  // warp-uniform
+    const uint64_t cta0 = (uint64_t)blockIdx.x * kBlock;
+    for (uint64_t c0 = cta0; c0 < e; c0 += p * U) {  // CTA-uniform
+      const uint64_t k0 = c0 + (gt - cta0) - lane;
       uint64_t k[U];
       bool ok[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) { k[u] = k0 + lane + (uint64_t)u * p; ok[u] = k[u] < e; }
       process(k, ok);
+      flush();
     }
   } else {
     // blocked: thread gt takes [gt * C, min(e, (gt + 1) * C)), C = ceil(e / p)
@@ -657,6 +674,7 @@ __global__ void __launch_bounds__(kBlock) k_lb(TravCtx c) {
 #pragma unroll
       for (int u = 0; u < U; ++u) { k[u] = lo + i0 + u; ok[u] = k[u] < hi; }
       process(k, ok);
+      flush();
     }
   }
 
