@@ -376,10 +376,15 @@ __device__ __forceinline__ void block_reduce_store(double l1, float dang, double
 // Sum of x/deg over the in-edges idx[b + o], idx[b + o + S], ... (< deg) of one vertex, in that
 // order. U index loads are issued before their U dependent gathers, so a thread keeps U requests
 // in flight; the index stream is read once (evict-first), the gathers go through the read-only path.
-template <int U>
+// kComp (the CTA bin): the U values of a step are added pairwise and the step sums are
+// accumulated with Kahan's compensation. A thread of a CTA-bin vertex adds up to
+// (threshold / block) terms, and a plain FP32 running sum over tens of thousands of them drifts
+// beyond the accuracy PageRank needs; a warp- or thread-bin thread adds at most 8 and keeps the
+// plain sum.
+template <int U, bool kComp>
 __device__ __forceinline__ float strided_sum(const uint32_t* __restrict__ idx, const float* __restrict__ cb,
                                              uint32_t b, uint32_t deg, uint32_t o, uint32_t S) {
-  float s = 0.0f;
+  float s = 0.0f, comp = 0.0f;
   for (uint32_t e0 = o; e0 < deg; e0 += S * U) {
     uint32_t id[U];
 #pragma unroll
@@ -390,9 +395,22 @@ __device__ __forceinline__ float strided_sum(const uint32_t* __restrict__ idx, c
     float v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) v[u] = id[u] != kInf ? __ldg(cb + id[u]) : 0.0f;
+    if constexpr (kComp) {
 #pragma unroll
-    for (int u = 0; u < U; ++u) s += v[u];
+      for (int w = 1; w < U; w <<= 1) {
+#pragma unroll
+        for (int u = 0; u + w < U; u += 2 * w) v[u] += v[u + w];
+      }
+      const float y = v[0] - comp;
+      const float t = s + y;
+      comp = (t - s) - y;
+      s = t;
+    } else {
+#pragma unroll
+      for (int u = 0; u < U; ++u) s += v[u];
+    }
   }
+  (void)comp;
   return s;
 }
 
@@ -401,7 +419,7 @@ constexpr uint32_t kCtaBatch = 32;  // CTA-bin vertices per barrier
 // CTA, warp and thread bins. Static assignment (CTA b always takes the same cost-balanced range
 // of items, and within it the same warp / thread takes the same vertex), fixed reduction order,
 // so sums and partials are reproducible.
-__global__ void __launch_bounds__(kBlock) k_pr_pull(PrCtx c) {
+__global__ void __launch_bounds__(kBlock, 8) k_pr_pull(PrCtx c) {
   __shared__ float s_part[kCtaBatch][kWarps + 1];
   const PrArgs* pa = c.args;
   const float d = pa->damping;
@@ -429,7 +447,7 @@ __global__ void __launch_bounds__(kBlock) k_pr_pull(PrCtx c) {
       if (j >= c_end) break;  // CTA-uniform
       const uint32_t v = items[j];
       const uint32_t b = c.off[v], deg = c.off[v + 1] - b;
-      float sv = strided_sum<4>(idx, cb, b, deg, tid, kBlock);
+      float sv = strided_sum<4, true>(idx, cb, b, deg, tid, kBlock);
       sv = warp_sum(sv);
       if (lane == 0) s_part[i][warp] = sv;
     }
@@ -453,7 +471,7 @@ __global__ void __launch_bounds__(kBlock) k_pr_pull(PrCtx c) {
   for (uint32_t j = cut[G1] + warp; j < w_end; j += kWarps) {
     const uint32_t v = items[j];
     const uint32_t b = c.off[v], deg = c.off[v + 1] - b;
-    float sv = warp_sum(strided_sum<4>(idx, cb, b, deg, lane, 32));
+    float sv = warp_sum(strided_sum<4, false>(idx, cb, b, deg, lane, 32));
     if (lane == 0) {
       pr_update(c, v, deg, sv, base, d, par, l1, dang);
       edges += deg;
@@ -464,7 +482,7 @@ __global__ void __launch_bounds__(kBlock) k_pr_pull(PrCtx c) {
   for (uint32_t j = cut[2 * G1] + tid; j < t_end; j += kBlock) {
     const uint32_t v = items[j];
     const uint32_t b = c.off[v], deg = c.off[v + 1] - b;
-    pr_update(c, v, deg, strided_sum<8>(idx, cb, b, deg, 0, 1), base, d, par, l1, dang);
+    pr_update(c, v, deg, strided_sum<8, false>(idx, cb, b, deg, 0, 1), base, d, par, l1, dang);
     edges += deg;
   }
   if (c.cta_twc) {
