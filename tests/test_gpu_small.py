@@ -521,3 +521,35 @@ def test_hub_updates_aggregated_per_cta():
     assert np.array_equal(host(o), oracle.sssp(g.n, g.offsets, g.indices, g.weights, hub))
     C.close()
     G.close()
+
+
+def test_tile_push_overflow_goes_to_the_frontier():
+    """A tile whose pushes exceed the CTA staging buffer (2048 entries): the centres of three
+    stars of 3,000-6,000 leaves sit in the CTA bin (threshold above their degree), so one tile
+    discovers thousands of vertices at once and the excess goes to the frontier directly. The
+    leaves are chained so later rounds and k-core peeling have work too."""
+    rng = np.random.Generator(np.random.Philox(key=11))
+    n = 20000
+    edges = []
+    for c, lo, hi in ((0, 10, 6010), (1, 6010, 9010), (2, 9010, 14010)):
+        edges += [(c, v) for v in range(lo, hi)]
+    edges += [(0, 1), (1, 2)]
+    edges += [(v, v + 1) for v in range(10, 14009)]
+    edges += [(int(a), int(b)) for a, b in rng.integers(0, n, size=(20000, 2))]
+    w = rng.integers(1, 101, size=len(edges))
+    g = gg.from_edges(n, edges, w, symmetrize=True)
+    G = make(g)
+    o = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    for t in (1 << 40, -1, 100):
+        G.set_params(hub_threshold=t)
+        G.bfs(0, o)
+        assert np.array_equal(host(o), oracle.bfs(g.n, g.offsets, g.indices, 0)), t
+        if t == 1 << 40:
+            assert G.stats()["pushes"] > 3 * 2048  # round 1 pushes the three stars' leaves
+        G.sssp(0, o)
+        assert np.array_equal(host(o), oracle.sssp(g.n, g.offsets, g.indices, g.weights, 0)), t
+        G.cc(o)
+        assert np.array_equal(host(o), oracle.cc(g.n, g.offsets, g.indices)), t
+        G.kcore(3, o)
+        assert np.array_equal(host(o), oracle.kcore(g.n, g.offsets, g.indices, 3)), t
+    G.close()
