@@ -93,7 +93,11 @@ typedef struct {
   uint32_t distribution;   /* LB edge distribution: 0 cyclic (default), 1 blocked (Sec. 4.1) */
   uint32_t exec_mode;      /* 0: device-side round loop in a CUDA graph (default); 1: host loop */
   uint32_t max_rounds;     /* 0: n + 1 (enough for every app); ALB_ERR_TIMEOUT when reached */
-  float l2_persist_fraction; /* share of L2 kept for the label array (0 = off, default) */
+  float l2_persist_fraction; /* > 0 (CUDA-graph mode): the labels get an L2 access-policy window
+                              * whose hits persist in this share of the device's persisting L2
+                              * maximum (set for the calling process's context); the labels are
+                              * then computed in the handle's buffer and copied to the output.
+                              * 0 = off (default) */
   uint32_t profile;        /* 1: time every kernel launch with CUDA events (host loop only) */
   uint32_t cta_stats;      /* 1: count the edges each CTA expands (alb_get_cta_loads) */
 } alb_params;

@@ -140,6 +140,35 @@ static alb_status add_kernel(cudaGraphNode_t* node, cudaGraph_t graph, const cud
 }
 
 // memset(state) -> init -> while(frontier non-empty) { inspect -> if(work) { lb } } [-> kcore finish]
+// L2 persistence for the label array (alb_params.l2_persist_fraction > 0, CUDA-graph mode): the
+// labels live in the handle's own buffer, whose address the cached graph can hold, and are copied
+// to the caller's buffer at the end of the call; the round kernels' nodes carry an access-policy
+// window over that buffer whose hits persist in the L2 set-aside (a share of the device's
+// persisting maximum, set for this process's context), while the streamed CSR goes through the
+// rest of L2 as usual.
+static bool persist_labels(const alb_graph g) {
+  return g->params.l2_persist_fraction > 0.f && g->params.exec_mode == 0;
+}
+
+static alb_status label_window(alb_graph g, cudaAccessPolicyWindow* w) {
+  int max_win = 0, max_persist = 0;
+  ALB_CUDA_TRY(cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, g->device));
+  ALB_CUDA_TRY(cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, g->device));
+  const size_t bytes = sizeof(uint32_t) * (size_t)g->n;
+  const size_t win = bytes < (size_t)max_win ? bytes : (size_t)max_win;
+  const size_t aside = (size_t)((double)g->params.l2_persist_fraction * (double)max_persist);
+  size_t cur = 0;
+  ALB_CUDA_TRY(cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize));
+  if (cur < aside) ALB_CUDA_TRY(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, aside));
+  w->base_ptr = g->tmp;
+  w->num_bytes = win;
+  // hits beyond the set-aside would evict each other: mark only that share of the window
+  w->hitRatio = win ? (float)(aside < win ? (double)aside / (double)win : 1.0) : 0.f;
+  w->hitProp = cudaAccessPropertyPersisting;
+  w->missProp = cudaAccessPropertyStreaming;
+  return ALB_OK;
+}
+
 static alb_status build_graph(alb_graph g, App app) {
   cudaGraph_t G = nullptr;
   ALB_CUDA_TRY(cudaGraphCreate(&G, 0));
@@ -179,6 +208,13 @@ static alb_status build_graph(alb_graph g, App app) {
   cudaGraph_t ifbody = ip.conditional.phGraph_out[0];
   if ((rc = add_kernel(&n_lb, ifbody, nullptr, 0, lb_fn(app), g->lb_blocks, &c)) != ALB_OK)
     return fail(rc);
+  if (persist_labels(g)) {
+    cudaKernelNodeAttrValue v{};
+    if ((rc = label_window(g, &v.accessPolicyWindow)) != ALB_OK) return fail(rc);
+    if (cudaGraphKernelNodeSetAttribute(n_insp, cudaKernelNodeAttributeAccessPolicyWindow, &v) != cudaSuccess ||
+        cudaGraphKernelNodeSetAttribute(n_lb, cudaKernelNodeAttributeAccessPolicyWindow, &v) != cudaSuccess)
+      return fail(ALB_ERR_CUDA);
+  }
   if (app == APP_KCORE) {
     cudaKernelNodeParams kp{};
     const CallArgs* ca = g->args;
@@ -276,8 +312,9 @@ static alb_status host_loop(alb_graph g, App app, cudaStream_t s) {
 alb_status run_traversal(alb_graph g, App app, uint32_t src, uint32_t k, uint32_t* out,
                          cudaStream_t s) {
   const bool dev = is_device_ptr(out);
+  const bool persist = persist_labels(g);
   uint32_t* lab = out;
-  if (!dev) {
+  if (!dev || persist) {
     alb_status rc = ensure_tmp(g);
     if (rc != ALB_OK) return rc;
     lab = g->tmp;
@@ -299,7 +336,9 @@ alb_status run_traversal(alb_graph g, App app, uint32_t src, uint32_t k, uint32_
     alb_status rc = host_loop(g, app, s);
     if (rc != ALB_OK) return rc;
   }
-  if (!dev) ALB_CUDA_TRY(cudaMemcpyAsync(out, lab, sizeof(uint32_t) * g->n, cudaMemcpyDeviceToHost, s));
+  if (lab != out)
+    ALB_CUDA_TRY(cudaMemcpyAsync(out, lab, sizeof(uint32_t) * g->n,
+                                 dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   ALB_CUDA_TRY(cudaGetLastError());
   g->last_stream = s;
   g->last_kind = 0;

@@ -553,3 +553,25 @@ def test_tile_push_overflow_goes_to_the_frontier():
         G.kcore(3, o)
         assert np.array_equal(host(o), oracle.kcore(g.n, g.offsets, g.indices, 3)), t
     G.close()
+
+
+@pytest.mark.parametrize("frac", [0.25, 1.0])
+def test_l2_persistence_window_keeps_results(rmat13, frac):
+    """l2_persist_fraction > 0: the labels are computed in the handle's buffer under an L2
+    access-policy window and copied out; results are unchanged, to device and host outputs."""
+    g = rmat13
+    src = g.max_degree_vertex()
+    G = make(g)
+    G.set_params(l2_persist_fraction=frac, hub_threshold=512)
+    o = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    G.bfs(src, o)
+    assert np.array_equal(host(o), oracle.bfs(g.n, g.offsets, g.indices, src))
+    G.sssp(src, o)
+    assert np.array_equal(host(o), oracle.sssp(g.n, g.offsets, g.indices, g.weights, src))
+    G.cc(o)
+    assert np.array_equal(host(o), oracle.cc(g.n, g.offsets, g.indices))
+    h = torch.empty(g.n, dtype=torch.int32).pin_memory()
+    G.kcore(3, h)
+    G.sync()
+    assert np.array_equal(h.numpy().view(np.uint32), oracle.kcore(g.n, g.offsets, g.indices, 3))
+    G.close()
