@@ -46,11 +46,12 @@ KERNEL_NAMES = {
     ("kcore", "twc"): "k_inspect<KcoreOp>", ("kcore", "lb"): "k_lb<KcoreOp>",
     ("pr", "twc"): "k_pr_pull", ("pr", "lb"): "k_pr_hub",
 }
-KERNEL_SOURCES = ["paper_1911_09135_gb300/csrc/alb/alb_traverse.cu",
-                  "paper_1911_09135_gb300/csrc/alb/alb_kernels.cuh",
-                  "paper_1911_09135_gb300/csrc/alb/alb_pagerank.cu",
-                  "paper_1911_09135_gb300/csrc/alb/alb_device.cuh",
-                  "paper_1911_09135_gb300/csrc/alb/alb_internal.cuh"]
+# the files that define each kernel family's device code (traffic.json is keyed to their hash)
+_CSRC = "paper_1911_09135_gb300/csrc/alb/"
+KERNEL_SOURCES = {
+    "k_pr_": [_CSRC + f for f in ("alb_pagerank.cu", "alb_device.cuh", "alb_internal.cuh")],
+    "k_": [_CSRC + f for f in ("alb_kernels.cuh", "alb_device.cuh", "alb_internal.cuh")],
+}
 
 
 def parse_args():
@@ -208,9 +209,11 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_src_sha() -> str:
+def kernel_src_sha(kernel: str) -> str:
+    """Hash of the sources that define `kernel` (by name prefix: PageRank's or the traversals')."""
+    files = next(v for k, v in KERNEL_SOURCES.items() if kernel.startswith(k))
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in files:
         h.update(open(os.path.join(ROOT, rel), "rb").read())
     return h.hexdigest()[:16]
 
@@ -222,7 +225,7 @@ def traffic_for(kernel: str, units: float):
         return None
     d = json.load(open(p))
     ent = d.get(kernel)
-    if not ent or ent.get("src_sha") != kernel_src_sha():
+    if not ent or ent.get("src_sha") != kernel_src_sha(kernel):
         return None
     return ent.get("dram_bytes_per_launch")
 
