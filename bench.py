@@ -799,6 +799,10 @@ def cta_load_arm(args, dist):
 
 def main():
     args = parse_args()
+    if args.workload == "serve":
+        # one hardware work queue per slot stream: with the default 8, several slots share a FIFO
+        # queue and a small graph's batch waits behind a large graph's (set before CUDA starts)
+        os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     dist = Dist()
     if args.workload == "cta-load":
         import torch

@@ -308,6 +308,30 @@ alb_status alb_get_cta_loads(alb_graph g, uint64_t* hd_twc, uint64_t* hd_lb, uin
 alb_status alb_debug_check(alb_graph g, uint32_t* out4);
 uint32_t alb_checked_build(void);
 
+/* ------------------------------------------------------- SM partitions (serving) */
+
+/* An SM partition: a CUDA green context owning a subset of the device's SMs. Kernels launched on
+ * a stream created from it (every call of this library takes the stream) run only on its SMs.
+ * A server gives small graphs a partition of their own, so their short round kernels do not wait
+ * for SM room held by large graphs' persistent round kernels. There is no counterpart in the
+ * paper, which runs one query at a time. Device memory is shared with the rest of the process.
+ * Returns ALB_ERR_UNSUPPORTED where the driver has no green contexts. */
+typedef struct alb_partition_s* alb_partition; /* opaque, library-owned */
+
+/* Split device `device` into *first with sm_count SMs (rounded up to the device's partition
+ * granularity, 8 SMs on GB300) and *rest with the remaining SMs. sm_count must leave SMs for
+ * *rest (ALB_ERR_INVALID_ARG otherwise; nothing is created). */
+alb_status alb_partition_split(int device, uint32_t sm_count, alb_partition* first, alb_partition* rest);
+/* SMs the partition owns. */
+alb_status alb_partition_sms(alb_partition p, uint32_t* sms);
+/* A non-blocking stream of the partition with the given priority (lower = higher, as
+ * cudaStreamCreateWithPriority); destroy it with alb_partition_stream_destroy before the
+ * partition. */
+alb_status alb_partition_stream_create(alb_partition p, int priority, alb_stream* out);
+alb_status alb_partition_stream_destroy(alb_stream s);
+/* Destroys the partition (its streams must be destroyed and their work complete). */
+alb_status alb_partition_destroy(alb_partition p);
+
 /* Library version: major * 10000 + minor * 100 + patch. */
 uint32_t alb_version(void);
 

@@ -30,6 +30,7 @@ ALB_SOURCES = [
     "alb/alb_pagerank.cu",
     "alb/alb_batch.cu",
     "alb/alb_tune.cu",
+    "alb/alb_partition.cu",
 ]
 ALB_HEADERS = [
     "alb/alb_internal.cuh",

@@ -35,6 +35,8 @@ EXPORTS = [
     "alb_sync", "alb_get_stats", "alb_status_str", "alb_version", "alb_bfs_noalloc",
     "alb_bfs_multi", "alb_sssp_multi", "alb_autotune", "alb_set_app_params", "alb_get_app_params",
     "alb_graph_clone", "alb_debug_check", "alb_checked_build", "alb_get_cta_loads",
+    "alb_partition_split", "alb_partition_sms", "alb_partition_stream_create",
+    "alb_partition_stream_destroy", "alb_partition_destroy",
 ]
 
 ALB_APP = {"bfs": 0, "sssp": 1, "cc": 2, "pr": 3, "pagerank": 3, "kcore": 4}
@@ -131,6 +133,11 @@ def load(build_if_missing: bool = False):
         "alb_status_str": ([S], ctypes.c_char_p),
         "alb_version": ([], _U32),
         "alb_bfs_noalloc": ([_U32, ctypes.c_uint64, _P, _P, _U32, _P, _P], S),
+        "alb_partition_split": ([S, _U32, ctypes.POINTER(_P), ctypes.POINTER(_P)], S),
+        "alb_partition_sms": ([_P, ctypes.POINTER(_U32)], S),
+        "alb_partition_stream_create": ([_P, S, ctypes.POINTER(_P)], S),
+        "alb_partition_stream_destroy": ([_P], S),
+        "alb_partition_destroy": ([_P], S),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -332,6 +339,44 @@ def alb_get_cta_loads(g, cap: int = 1 << 16):
     _check(load().alb_get_cta_loads(g, twc.ctypes.data, lb.ctypes.data, cap, ctypes.byref(nt),
                                     ctypes.byref(nl)), "alb_get_cta_loads")
     return twc[:min(cap, nt.value)], lb[:min(cap, nl.value)]
+
+
+class Partition:
+    """An SM partition (alb_partition_split): streams made from it run kernels on its SMs only."""
+
+    def __init__(self, handle: int):
+        self.h = handle
+        self._streams = []
+
+    @property
+    def sms(self) -> int:
+        n = _U32(0)
+        _check(load().alb_partition_sms(self.h, ctypes.byref(n)), "alb_partition_sms")
+        return int(n.value)
+
+    def stream(self, priority: int = 0) -> int:
+        """A new non-blocking stream of the partition (a cudaStream_t as int), owned by it."""
+        s = _P()
+        _check(load().alb_partition_stream_create(self.h, priority, ctypes.byref(s)),
+               "alb_partition_stream_create")
+        self._streams.append(s.value)
+        return int(s.value)
+
+    def close(self):
+        for s in self._streams:
+            load().alb_partition_stream_destroy(s)
+        self._streams = []
+        if self.h:
+            load().alb_partition_destroy(self.h)
+            self.h = None
+
+
+def partition_split(device: int, sm_count: int):
+    """(first, rest): device split into sm_count SMs (rounded up) and the remaining SMs."""
+    a, b = _P(), _P()
+    _check(load().alb_partition_split(device, sm_count, ctypes.byref(a), ctypes.byref(b)),
+           "alb_partition_split")
+    return Partition(a.value), Partition(b.value)
 
 
 def alb_checked_build() -> int:

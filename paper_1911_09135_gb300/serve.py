@@ -16,6 +16,13 @@ arrive meanwhile wait for the next batch of their graph. A request's latency run
 arrival to the completion of its result's device-to-host copy.
 
 All traversal work runs in libalb.so; this module only schedules calls.
+
+The device multiplexes streams onto CUDA_DEVICE_MAX_CONNECTIONS hardware work queues (8 by
+default): slots whose streams share a queue run in its FIFO order, so a small graph's batch waits
+behind a large graph's. A serving process sets CUDA_DEVICE_MAX_CONNECTIONS=32 before CUDA starts
+(the server warns when it has more slots than queues). `small_sms` instead gives the small graphs
+an SM partition of their own (a green context, alb_partition_split); it is off by default: with
+enough queues the SMs are shared well, and a fixed partition measured slower.
 """
 from __future__ import annotations
 
@@ -63,10 +70,12 @@ def poisson_requests(graphs, count: int, rate: float, seed: int = 5) -> list[Req
 class _Slot:
     """One handle (the graph's own, or a clone sharing its CSR) with its stream and buffers."""
 
-    def __init__(self, torch, G, n, priority: int):
+    def __init__(self, torch, G, n, priority: int, part=None):
         self.G = G
         self.n = n
-        self.stream = torch.cuda.Stream(priority=priority)
+        # a stream of the graph's SM partition, else an ordinary one
+        self.stream = (torch.cuda.ExternalStream(part.stream(priority)) if part is not None
+                       else torch.cuda.Stream(priority=priority))
         self.busy = None      # (event, batch info) while a batch is in flight
         # Result buffers of one batch, allocated once: nothing is allocated while other slots'
         # kernels run (an allocation can wait for the whole device).
@@ -97,7 +106,8 @@ class _Graph:
         multi-source workspace (148 bytes per vertex) and the round workspace (20 per vertex)."""
         return n * (4 * (2 * GROUP + 1) + 148 + 20)
 
-    def __init__(self, torch, csr, tune: bool, slots: int, priority: int, ctas_per_sm: int = 2):
+    def __init__(self, torch, csr, tune: bool, slots: int, priority: int, ctas_per_sm: int = 2,
+                 part=None):
         self.n = csr.n
         self.m = csr.m
         self.deg = csr.degrees().astype(np.int64)
@@ -107,7 +117,8 @@ class _Graph:
         # A persistent grid over the whole GPU would keep other slots' kernels waiting until it
         # ends: small graphs get a grid sized to their edges, large ones two CTAs per SM, so
         # kernels of several slots share the SMs.
-        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        sms = (part.sms if part is not None else
+               torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
         G.set_params(grid_blocks=min(ctas_per_sm * sms, max(16, -(-csr.m // EDGES_PER_CTA))))
         if tune:
             src = int(np.argmax(self.deg))
@@ -119,7 +130,7 @@ class _Graph:
             if free < 2 * self.slot_bytes(csr.n) + (1 << 30):
                 break
             handles.append(G.clone())  # clones keep the tuned knobs
-        self.slots = [_Slot(torch, h, csr.n, priority) for h in handles]
+        self.slots = [_Slot(torch, h, csr.n, priority, part) for h in handles]
         for sl in self.slots:
             sl.warm(int(np.argmax(self.deg)))
         self.queue = {k: deque() for k in KINDS}
@@ -139,16 +150,33 @@ class Server:
 
     def __init__(self, graphs, *, tune: bool = True, keep_results: bool = False,
                  hbm_reserve: int = 1 << 30, big_graph_edges: int = 50_000_000, big_slots: int = 2,
-                 ctas_per_sm: int = 2):
+                 ctas_per_sm: int = 2, small_sms: int = 0):
         import torch
         self.torch = torch
+        # small_sms > 0: the graphs below big_graph_edges get an SM partition of that many SMs and
+        # the large graphs the rest, so small graphs' round kernels never wait for SM room held
+        # by the large graphs' persistent kernels
+        self.parts = None
+        if small_sms > 0:
+            self.parts = alb.partition_split(torch.cuda.current_device(), small_sms)
         # smaller graphs get higher stream priority, so their short rounds are scheduled
         # between the round kernels of large graphs instead of waiting behind them
         lo, hi = torch.cuda.Stream.priority_range()
         order = np.argsort(np.argsort([g.m for g in graphs]))
         prio = [hi if order[i] < len(graphs) // 2 else lo for i in range(len(graphs))]
-        self.graphs = [_Graph(torch, g, tune, big_slots if g.m >= big_graph_edges else 1, prio[i], ctas_per_sm)
+        def part_of(g):
+            if self.parts is None:
+                return None
+            return self.parts[1] if g.m >= big_graph_edges else self.parts[0]
+        self.graphs = [_Graph(torch, g, tune, big_slots if g.m >= big_graph_edges else 1, prio[i], ctas_per_sm,
+                              part_of(g))
                        for i, g in enumerate(graphs)]
+        slots = sum(len(g.slots) for g in self.graphs)
+        queues = int(os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS", "8"))
+        if slots + 1 > queues:
+            import warnings
+            warnings.warn(f"{slots} slot streams share {queues} hardware work queues; set "
+                          f"CUDA_DEVICE_MAX_CONNECTIONS={min(32, slots + 1)} before CUDA starts")
         self.keep = keep_results
         self.reserve = hbm_reserve
         self.results: dict[int, np.ndarray] = {}
@@ -159,8 +187,22 @@ class Server:
         self.checked = os.environ.get("ALB_CHECKED") == "1" and alb.alb_checked_build() == 1
 
     def close(self):
+        torch = self.torch
+        torch.cuda.synchronize()
         for g in self.graphs:
             g.close()
+        if self.parts is not None:
+            # the partitions' streams go last: first the buffers used on them, and the blocks the
+            # caching allocator may still associate with them
+            for g in self.graphs:
+                g.slots = []
+            import gc
+            gc.collect()
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+            for p in self.parts:
+                p.close()
+            self.parts = None
 
     def _free_bytes(self) -> int:
         free, _ = self.torch.cuda.mem_get_info()

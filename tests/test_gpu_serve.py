@@ -20,9 +20,12 @@ def graphs():
             for i, sc in enumerate((8, 10, 11, 13))]
 
 
-def test_results_alone_equal_results_in_the_mix(graphs):
+@pytest.mark.parametrize("small_sms", [0, 16])
+def test_results_alone_equal_results_in_the_mix(graphs, small_sms):
+    """Also with the small graphs on an SM partition of their own (small_sms > 0)."""
     reqs = serve.poisson_requests(graphs, 400, rate=20000.0, seed=5)
-    srv = serve.Server(graphs, tune=False, keep_results=True, big_graph_edges=100_000)
+    srv = serve.Server(graphs, tune=False, keep_results=True, big_graph_edges=100_000,
+                       small_sms=small_sms)
     try:
         assert len(srv.graphs[-1].slots) == 2            # a large graph gets a second slot (a clone)
         srv.run(reqs, realtime=True, timeout=120)
@@ -60,3 +63,33 @@ def test_admission_waits_for_free_device_memory(graphs):
         assert all(r.done >= 0 for r in reqs)
     finally:
         srv.close()
+
+
+def test_sm_partition_streams_run_the_library_exactly(graphs):
+    """Streams of both halves of an SM split run every app exactly (kernels, CUDA graphs with
+    device-side loops); the halves cover the device."""
+    from paper_1911_09135_gb300 import alb
+    first, rest = alb.partition_split(torch.cuda.current_device(), 16)
+    try:
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        assert first.sms >= 16 and first.sms + rest.sms == sms
+        g = graphs[-1]
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
+        G = alb.Graph(g.n, dev(g.offsets), dev(g.indices), dev(g.weights), symmetric=True)
+        o = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        src = g.max_degree_vertex()
+        for part in (first, rest):
+            s = torch.cuda.ExternalStream(part.stream())
+            with torch.cuda.stream(s):
+                alb.alb_bfs(G.h, src, o, s)
+                s.synchronize()
+                assert np.array_equal(o.cpu().numpy().view(np.uint32), oracle.bfs(g.n, g.offsets, g.indices, src))
+                alb.alb_sssp(G.h, src, o, s)
+                s.synchronize()
+                assert np.array_equal(o.cpu().numpy().view(np.uint32),
+                                      oracle.sssp(g.n, g.offsets, g.indices, g.weights, src))
+        G.close()
+    finally:
+        torch.cuda.synchronize()
+        first.close()
+        rest.close()
