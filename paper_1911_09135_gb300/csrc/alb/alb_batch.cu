@@ -219,7 +219,18 @@ __global__ void k_multi_seed(TravCtx c) {
 
 enum BatchKind { BK_MS_BFS = 0, BK_MS_SSSP = 1, BK_MULTI_BFS = 2, BK_MULTI_SSSP = 3, BK_COUNT = 4 };
 
+// Groups of 32 sources in flight at once: the handle and up to kBatchWorkers - 1 worker clones
+// (sharing its CSR, each with its own workspace and stream). One group's early and late rounds
+// have small frontiers and leave most of the device idle; groups on several streams fill it.
+constexpr uint32_t kBatchWorkers = 4;
+
 struct BatchWs {
+  alb_graph worker[kBatchWorkers - 1] = {};
+  cudaStream_t wstream[kBatchWorkers - 1] = {};
+  cudaEvent_t ev_start = nullptr;
+  cudaEvent_t ev_done[kBatchWorkers - 1] = {};
+  uint32_t nworkers = 0;       // created (and warmed)
+  uint32_t used_workers = 0;   // used by the last call (alb_sync checks them)
   uint32_t* lab = nullptr;
   uint32_t* seen = nullptr;
   unsigned long long* act = nullptr;
@@ -236,6 +247,12 @@ namespace alb {
 alb_status free_batch(alb_graph g) {
   BatchWs* b = g->batch;
   if (!b) return ALB_OK;
+  for (uint32_t w = 0; w < kBatchWorkers - 1; ++w) {  // callers synchronise the device first
+    if (b->worker[w]) alb_graph_destroy(b->worker[w]);
+    if (b->wstream[w]) cudaStreamDestroy(b->wstream[w]);
+    if (b->ev_done[w]) cudaEventDestroy(b->ev_done[w]);
+  }
+  if (b->ev_start) cudaEventDestroy(b->ev_start);
   for (int i = 0; i < BK_COUNT; ++i) {
     if (b->exec[i]) cudaGraphExecDestroy(b->exec[i]);
     if (b->graph[i]) cudaGraphDestroy(b->graph[i]);
@@ -253,6 +270,19 @@ alb_status free_batch(alb_graph g) {
 }
 
 alb_status batch_stats(alb_graph, alb_stats*) { return ALB_OK; }
+
+// Status of the worker clones used by the last batch call (their round limits and checks).
+alb_status batch_sync_workers(alb_graph g) {
+  BatchWs* b = g->batch;
+  alb_status rc = ALB_OK;
+  if (!b) return rc;
+  for (uint32_t w = 0; w < b->used_workers; ++w) {
+    const alb_status r = alb_sync(b->worker[w]);
+    if (rc == ALB_OK) rc = r;
+  }
+  b->used_workers = 0;
+  return rc;
+}
 
 static __global__ void k_set_aux(BatchAux* dst, BatchAux v) { *dst = v; }
 
@@ -382,6 +412,50 @@ static alb_status stage_srcs(alb_graph g, const uint32_t* hd_srcs, uint32_t k, c
   return ALB_OK;
 }
 
+// One group of ns <= 32 sources (device list) on handle h and stream s, into dst (device).
+static alb_status run_group_on(alb_graph h, BatchKind kind, const uint32_t* d_srcs, uint32_t ns, uint32_t* dst,
+                               cudaStream_t s) {
+  BatchWs* b = h->batch;
+  CallArgs ca{dst, 0u, 0u, nullptr, nullptr, nullptr, b->aux, d_srcs, ns};
+  k_set_args<<<1, 1, 0, s>>>(h->args, ca);
+  ALB_CUDA_TRY(cudaGetLastError());
+  ALB_CUDA_TRY(cudaGraphLaunch(b->exec[kind], s));
+  h->last_stream = s;
+  h->last_kind = 0;
+  return ALB_OK;
+}
+
+// Create (once) and warm `want` worker clones for `kind`: their workspaces and CUDA graphs exist
+// before any of them runs, and the device is idle while they are made (a first call that
+// allocates and instantiates while other streams run is avoided, as for serving slots).
+static alb_status ensure_workers(alb_graph g, BatchKind kind, int app, uint32_t want) {
+  BatchWs* b = g->batch;
+  bool made = false;
+  for (uint32_t w = 0; w < want; ++w) {
+    if (!b->worker[w]) {
+      if (!made) ALB_CUDA_TRY(cudaDeviceSynchronize());
+      made = true;
+      alb_status rc = alb_graph_clone(g, &b->worker[w]);
+      if (rc != ALB_OK) return rc;
+      ALB_CUDA_TRY(cudaStreamCreateWithFlags(&b->wstream[w], cudaStreamNonBlocking));
+      ALB_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_done[w], cudaEventDisableTiming));
+    }
+    alb_graph h = b->worker[w];
+    select_cfg(h, app);
+    if (!h->batch || !h->batch->lab || !h->batch->exec[kind]) {
+      if (!made) ALB_CUDA_TRY(cudaDeviceSynchronize());
+      made = true;
+      alb_status rc = ensure_batch(h, true, 0u, b->wstream[w]);
+      if (rc == ALB_OK && !h->batch->exec[kind]) rc = build_batch_graph(h, kind);
+      if (rc != ALB_OK) return rc;
+    }
+  }
+  if (!b->ev_start) ALB_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_start, cudaEventDisableTiming));
+  if (made) ALB_CUDA_TRY(cudaDeviceSynchronize());
+  if (want > b->nworkers) b->nworkers = want;
+  return ALB_OK;
+}
+
 static alb_status run_groups(alb_graph g, BatchKind kind, const uint32_t* hd_srcs, uint32_t k,
                              uint32_t* out, cudaStream_t s) {
   alb_status rc = ensure_batch(g, true, k, s);
@@ -390,8 +464,35 @@ static alb_status run_groups(alb_graph g, BatchKind kind, const uint32_t* hd_src
   if ((rc = stage_srcs(g, hd_srcs, k, s)) != ALB_OK) return rc;
   if (!b->exec[kind] && (rc = build_batch_graph(g, kind)) != ALB_OK) return rc;
   const bool dev = is_device_ptr(out);
-  if (!dev && !b->tmp) ALB_CUDA_TRY(cudaMalloc((void**)&b->tmp, sizeof(uint32_t) * (size_t)g->n * 32u));
   const size_t n = g->n;
+  const uint32_t ngroups = (k + 31u) / 32u;
+  b->used_workers = 0;
+  if (dev && ngroups > 1) {
+    // several groups with a device output: deal them over the handle and its worker clones
+    const uint32_t W = ngroups < kBatchWorkers ? ngroups : kBatchWorkers;
+    const int app = kind == BK_MS_BFS ? ALB_APP_BFS : ALB_APP_SSSP;
+    alb_status rc2 = ensure_workers(g, kind, app, W - 1);
+    if (rc2 != ALB_OK) return rc2;
+    select_cfg(g, app);
+    ALB_CUDA_TRY(cudaEventRecord(b->ev_start, s));
+    for (uint32_t w = 0; w + 1 < W; ++w) ALB_CUDA_TRY(cudaStreamWaitEvent(b->wstream[w], b->ev_start, 0));
+    for (uint32_t gi = 0; gi < ngroups; ++gi) {
+      const uint32_t w = gi % W, g0 = 32u * gi;
+      const uint32_t ns = (k - g0) < 32u ? (k - g0) : 32u;
+      alb_graph h = w == 0 ? g : b->worker[w - 1];
+      cudaStream_t hs = w == 0 ? s : b->wstream[w - 1];
+      if ((rc2 = run_group_on(h, kind, b->srcs + g0, ns, out + (size_t)g0 * n, hs)) != ALB_OK) return rc2;
+    }
+    for (uint32_t w = 0; w + 1 < W; ++w) {
+      ALB_CUDA_TRY(cudaEventRecord(b->ev_done[w], b->wstream[w]));
+      ALB_CUDA_TRY(cudaStreamWaitEvent(s, b->ev_done[w], 0));
+    }
+    b->used_workers = W - 1;
+    g->last_stream = s;
+    g->last_kind = 0;
+    return ALB_OK;
+  }
+  if (!dev && !b->tmp) ALB_CUDA_TRY(cudaMalloc((void**)&b->tmp, sizeof(uint32_t) * (size_t)g->n * 32u));
   for (uint32_t g0 = 0; g0 < k; g0 += 32u) {
     const uint32_t ns = (k - g0) < 32u ? (k - g0) : 32u;
     uint32_t* dst = dev ? out + (size_t)g0 * n : b->tmp;

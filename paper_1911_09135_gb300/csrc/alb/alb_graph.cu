@@ -430,7 +430,8 @@ alb_status alb_sync(alb_graph g) {
     alb_stats tmp{};
     batch_stats(g, &tmp);
   }
-  alb_status rc = g->latched;
+  const alb_status rw = batch_sync_workers(g);
+  alb_status rc = g->latched != ALB_OK ? g->latched : rw;
   g->latched = ALB_OK;
   return rc;
 }

@@ -188,6 +188,7 @@ alb_status launch_inspect_only(alb_graph g, const uint32_t* d_wl, uint32_t nf, u
 void occupancy(uint32_t* inspect_per_sm, uint32_t* lb_per_sm);
 alb_status pr_stats(alb_graph g, alb_stats* out);
 alb_status batch_stats(alb_graph g, alb_stats* out);
+alb_status batch_sync_workers(alb_graph g);  // status of the worker clones of the last batch call
 alb_status latch_from_state(alb_graph g, uint32_t status);
 uint32_t effective_threshold(alb_graph g);
 void select_cfg(alb_graph g, int app);

@@ -575,3 +575,51 @@ def test_l2_persistence_window_keeps_results(rmat13, frac):
     G.sync()
     assert np.array_equal(h.numpy().view(np.uint32), oracle.kcore(g.n, g.offsets, g.indices, 3))
     G.close()
+
+
+def test_batch_groups_run_concurrently_on_worker_clones(rmat13):
+    """130 sources = five groups (the last ragged) dealt over the handle and three worker clones
+    on their own streams; the same after a parameter change (the workers are rebuilt) and with
+    the ragged group first in a second call of 33 sources."""
+    g = rmat13
+    G = make(g)
+    rng = np.random.default_rng(21)
+    srcs = rng.integers(0, g.n, size=130).astype(np.uint32)
+    out = torch.empty(len(srcs) * g.n, dtype=torch.int32, device="cuda")
+    for params in (dict(), dict(hub_threshold=64), dict(exec_mode=1)):
+        G.set_params(**{"hub_threshold": -1, "exec_mode": 0, **params})
+        G.bfs_batch(srcs, out)
+        lv = host(out).reshape(len(srcs), g.n).copy()
+        G.sssp_batch(srcs, out)
+        ds = host(out).reshape(len(srcs), g.n).copy()
+        G.sync()
+        for i in range(0, len(srcs), 7):
+            s = int(srcs[i])
+            assert np.array_equal(lv[i], oracle.bfs(g.n, g.offsets, g.indices, s)), (params, i)
+            assert np.array_equal(ds[i], oracle.sssp(g.n, g.offsets, g.indices, g.weights, s)), (params, i)
+        assert np.array_equal(lv[129], oracle.bfs(g.n, g.offsets, g.indices, int(srcs[129])))
+    G.bfs_batch(srcs[:33], out)
+    lv = host(out)[:33 * g.n].reshape(33, g.n)
+    assert np.array_equal(lv[32], oracle.bfs(g.n, g.offsets, g.indices, int(srcs[32])))
+    G.close()
+
+
+def test_batch_worker_round_limit_reaches_sync():
+    """A round limit hit only by a group that runs on a worker clone is reported by alb_sync of
+    the handle: group 0 (on the handle) holds isolated vertices, group 1 (on a worker) walks a
+    path longer than the limit."""
+    n = 100
+    g = gg.from_edges(n, [(v, v + 1) for v in range(40, 99)], symmetrize=True)
+    G = make(g)
+    G.set_params(max_rounds=5)
+    srcs = np.array(list(range(32)) + [40], dtype=np.uint32)
+    out = torch.empty(len(srcs) * g.n, dtype=torch.int32, device="cuda")
+    G.bfs_batch(srcs, out)
+    with pytest.raises(alb.AlbError) as e:
+        G.sync()
+    assert e.value.code == 4
+    G.set_params(max_rounds=0)
+    G.bfs_batch(srcs, out)
+    G.sync()
+    assert np.array_equal(host(out)[32 * n:33 * n], oracle.bfs(g.n, g.offsets, g.indices, 40))
+    G.close()
