@@ -93,3 +93,18 @@ def test_sm_partition_streams_run_the_library_exactly(graphs):
         torch.cuda.synchronize()
         first.close()
         rest.close()
+
+
+def test_sm_partition_argument_errors():
+    from paper_1911_09135_gb300 import alb
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    for bad in (0, sms, sms + 8):
+        with pytest.raises(alb.AlbError) as e:
+            alb.partition_split(torch.cuda.current_device(), bad)
+        assert e.value.code == 1  # ALB_ERR_INVALID_ARG: nothing is created
+    first, rest = alb.partition_split(torch.cuda.current_device(), 1)   # rounded up to the granularity
+    try:
+        assert first.sms >= 1 and first.sms % 8 == 0 and first.sms + rest.sms == sms
+    finally:
+        first.close()
+        rest.close()
