@@ -370,6 +370,13 @@ static __device__ __forceinline__ void hub_append(bool huge, uint32_t v, uint32_
 
 // ----------------------------------------------------- inspection + TWC kernel
 
+// Resident CTAs per SM the round kernels are compiled for: 5 for the single-source operators
+// (the register cap costs a few spilled bytes, the extra warps hide more of the per-edge
+// latency chain: +8 % over bfs, sssp, cc and k-core on rmat24-hubs); the multi-source operators
+// hold a row of labels per edge and keep their registers.
+template <class Op>
+constexpr int round_kernel_min_blocks() { return Op::kBatch ? 1 : 5; }
+
 // Edges relaxed per thread per step (memory requests a thread keeps in flight), per bin.
 constexpr int kUCta = 8;     // CTA bin
 constexpr int kUWarp = 8;    // warp bin
@@ -377,7 +384,7 @@ constexpr int kUThread = 4;  // thread bin (fine-grained gather)
 constexpr int kULb = 8;      // LB kernel
 
 template <class Op>
-__global__ void __launch_bounds__(kBlock) k_inspect(TravCtx c) {
+__global__ void __launch_bounds__(kBlock, round_kernel_min_blocks<Op>()) k_inspect(TravCtx c) {
   __shared__ uint32_t s_cb[kBlock], s_cd[kBlock], s_cv[kBlock];       // CTA bin
   __shared__ uint32_t s_wb[kBlock], s_wd[kBlock], s_wv[kBlock];       // warp bin
   __shared__ uint32_t s_scan[kBlock + 1], s_sb[kBlock], s_sv[kBlock];  // thread bin
@@ -547,7 +554,7 @@ __global__ void __launch_bounds__(kBlock) k_inspect(TravCtx c) {
 struct TraceOp {};
 
 template <class Op, bool kTrace>
-__global__ void __launch_bounds__(kBlock) k_lb(TravCtx c) {
+__global__ void __launch_bounds__(kBlock, round_kernel_min_blocks<Op>()) k_lb(TravCtx c) {
   constexpr int kStage = kHubSmem;
   __shared__ uint32_t s_p[kStage];
   __shared__ uint32_t s_base[kStage];
