@@ -358,6 +358,19 @@ static alb_status build_batch_graph(alb_graph g, BatchKind kind) {
       seed_grid = g->blocks; seed_block = kBlock;
       break;
   }
+  // the round kernels' persistent grids from their own residency (the multi-source operators
+  // hold more registers than the single-source ones the handle's grids are sized for); the
+  // paper's threshold rule follows this LB grid
+  uint32_t ib = g->blocks, lbb = g->lb_blocks;
+  if (!g->params.grid_blocks) {
+    int bi = 0, bl = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bi, insp, kBlock, 0) == cudaSuccess && bi > 0)
+      ib = (uint32_t)g->num_sms * (uint32_t)bi;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, lb, kBlock, 0) == cudaSuccess && bl > 0)
+      lbb = (uint32_t)g->num_sms * (uint32_t)bl;
+    cudaGetLastError();
+    if (g->params.hub_threshold < 0) c.threshold = lbb * (uint32_t)kBlock;
+  }
   cudaGraphNode_t n_ms, n_init, n_seed, n_while, n_insp, n_if, n_lb, n_out;
   cudaMemsetParams ms{};
   ms.dst = g->st;
@@ -376,14 +389,14 @@ static alb_status build_batch_graph(alb_graph g, BatchKind kind) {
   wp.conditional.size = 1;
   if (cudaGraphAddNode(&n_while, G, &n_seed, nullptr, 1, &wp) != cudaSuccess) return fail(ALB_ERR_CUDA);
   cudaGraph_t body = wp.conditional.phGraph_out[0];
-  if ((rc = add_node(&n_insp, body, nullptr, 0, insp, g->blocks, kBlock, &c)) != ALB_OK) return fail(rc);
+  if ((rc = add_node(&n_insp, body, nullptr, 0, insp, ib, kBlock, &c)) != ALB_OK) return fail(rc);
   cudaGraphNodeParams ip{};
   ip.type = cudaGraphNodeTypeConditional;
   ip.conditional.handle = hi;
   ip.conditional.type = cudaGraphCondTypeIf;
   ip.conditional.size = 1;
   if (cudaGraphAddNode(&n_if, body, &n_insp, nullptr, 1, &ip) != cudaSuccess) return fail(ALB_ERR_CUDA);
-  if ((rc = add_node(&n_lb, ip.conditional.phGraph_out[0], nullptr, 0, lb, g->lb_blocks, kBlock, &c)) != ALB_OK)
+  if ((rc = add_node(&n_lb, ip.conditional.phGraph_out[0], nullptr, 0, lb, lbb, kBlock, &c)) != ALB_OK)
     return fail(rc);
   if (kind == BK_MS_BFS || kind == BK_MS_SSSP) {
     if ((rc = add_node(&n_out, G, &n_while, 1, (void*)k_batch_out, g->blocks, kBlock, &c)) != ALB_OK)

@@ -372,10 +372,11 @@ static __device__ __forceinline__ void hub_append(bool huge, uint32_t v, uint32_
 
 // Resident CTAs per SM the round kernels are compiled for: 5 for the single-source operators
 // (the register cap costs a few spilled bytes, the extra warps hide more of the per-edge
-// latency chain: +8 % over bfs, sssp, cc and k-core on rmat24-hubs); the multi-source operators
-// hold a row of labels per edge and keep their registers.
+// latency chain: +8 % over bfs, sssp, cc and k-core on rmat24-hubs); 4 for the multi-source
+// operators, which hold a row of labels per edge (5 spilled up to 272 bytes; with no minimum,
+// ptxas gave them up to 118 registers and 2 CTAs per SM, 1.4x slower batches).
 template <class Op>
-constexpr int round_kernel_min_blocks() { return Op::kBatch ? 1 : 5; }
+constexpr int round_kernel_min_blocks() { return Op::kBatch ? 4 : 5; }
 
 // Edges relaxed per thread per step (memory requests a thread keeps in flight), per bin.
 constexpr int kUCta = 8;     // CTA bin
