@@ -383,6 +383,7 @@ constexpr int kUCta = 8;     // CTA bin
 constexpr int kUWarp = 8;    // warp bin
 constexpr int kUThread = 4;  // thread bin (fine-grained gather)
 constexpr int kULb = 8;      // LB kernel
+constexpr int kUMs = 8;      // multi-source operators (every bin and the LB kernel)
 
 template <class Op>
 __global__ void __launch_bounds__(kBlock, round_kernel_min_blocks<Op>()) k_inspect(TravCtx c) {
@@ -391,6 +392,9 @@ __global__ void __launch_bounds__(kBlock, round_kernel_min_blocks<Op>()) k_inspe
   __shared__ uint32_t s_scan[kBlock + 1], s_sb[kBlock], s_sv[kBlock];  // thread bin
   __shared__ uint32_t s_warp[kWarps + 1];
   __shared__ uint32_t s_ncta, s_nwrp, s_tile;
+  constexpr int UC = Op::kBatch ? kUMs : kUCta;  // edges in flight per thread, per bin
+  constexpr int UW = Op::kBatch ? kUMs : kUWarp;
+  constexpr int UT = Op::kBatch ? (kUMs < kUThread ? kUMs : kUThread) : kUThread;
   __shared__ uint32_t s_push[kPushBuf];  // the tile's pushes (PushSink)
   __shared__ uint32_t s_npush, s_pbase;
   constexpr bool kHot = aggregates<Op>::value;
@@ -475,41 +479,41 @@ __global__ void __launch_bounds__(kBlock, round_kernel_min_blocks<Op>()) k_inspe
     const uint32_t ncta = s_ncta;
     for (uint32_t j = 0; j < ncta; ++j) {
       const uint32_t b = s_cb[j], d = s_cd[j], svj = s_cv[j];
-      for (uint32_t e0 = 0; e0 < d; e0 += kBlock * kUCta) {
-        uint32_t e[kUCta], s4[kUCta];
-        bool ok[kUCta];
+      for (uint32_t e0 = 0; e0 < d; e0 += kBlock * UC) {
+        uint32_t e[UC], s4[UC];
+        bool ok[UC];
 #pragma unroll
-        for (int u = 0; u < kUCta; ++u) {
+        for (int u = 0; u < UC; ++u) {
           const uint32_t q = e0 + u * kBlock + tid;
           ok[u] = q < d; e[u] = b + q; s4[u] = svj;
         }
-        relax<Op, kUCta>(c, a, e, ok, s4, sink, hk, hc);
+        relax<Op, UC>(c, a, e, ok, s4, sink, hk, hc);
       }
     }
     // Warp bin: one warp per vertex.
     const uint32_t nw = s_nwrp;
     for (uint32_t j = warp; j < nw; j += kWarps) {
       const uint32_t b = s_wb[j], d = s_wd[j], svj = s_wv[j];
-      for (uint32_t e0 = 0; e0 < d; e0 += 32 * kUWarp) {
-        uint32_t e[kUWarp], s4[kUWarp];
-        bool ok[kUWarp];
+      for (uint32_t e0 = 0; e0 < d; e0 += 32 * UW) {
+        uint32_t e[UW], s4[UW];
+        bool ok[UW];
 #pragma unroll
-        for (int u = 0; u < kUWarp; ++u) {
+        for (int u = 0; u < UW; ++u) {
           const uint32_t q = e0 + u * 32 + lane;
           ok[u] = q < d; e[u] = b + q; s4[u] = svj;
         }
-        relax<Op, kUWarp>(c, a, e, ok, s4, sink, hk, hc);
+        relax<Op, UW>(c, a, e, ok, s4, sink, hk, hc);
       }
     }
     // Thread bin: the small vertices' edges, gathered over the whole CTA
     // (consecutive threads take consecutive edges of the concatenated lists).
     const uint32_t S = s_scan[kBlock];
     uint32_t owner = 0u;
-    for (uint32_t q0 = 0; q0 < S; q0 += kBlock * kUThread) {
-      uint32_t e[kUThread], s2[kUThread];
-      bool ok[kUThread];
+    for (uint32_t q0 = 0; q0 < S; q0 += kBlock * UT) {
+      uint32_t e[UT], s2[UT];
+      bool ok[UT];
 #pragma unroll
-      for (int u = 0; u < kUThread; ++u) {
+      for (int u = 0; u < UT; ++u) {
         const uint32_t q = q0 + u * kBlock + tid;
         ok[u] = q < S;
         e[u] = 0u; s2[u] = 0u;
@@ -519,7 +523,7 @@ __global__ void __launch_bounds__(kBlock, round_kernel_min_blocks<Op>()) k_inspe
           s2[u] = s_sv[owner];
         }
       }
-      relax<Op, kUThread>(c, a, e, ok, s2, sink, hk, hc);
+      relax<Op, UT>(c, a, e, ok, s2, sink, hk, hc);
     }
     __syncthreads();
     push_flush(sink, &s_pbase);
@@ -581,7 +585,7 @@ __global__ void __launch_bounds__(kBlock, round_kernel_min_blocks<Op>()) k_lb(Tr
   const OpArgs a{ca->lab, c.pushed ? c.pushed + (size_t)cur * c.pw : nullptr, r + 1u, ca->k, ca->aux, c.n, c.chk};
   const uint32_t tid = threadIdx.x, lane = tid & 31u;
   // a step of the CTA is kBlock x U positions, at most one push each: the buffer never overflows
-  static_assert(kTrace || kBlock * kULb <= kPushBuf, "one LB step's pushes must fit the CTA buffer");
+  static_assert(kTrace || kBlock * U <= kPushBuf, "one LB step's pushes must fit the CTA buffer");
   const PushSink sink{Fn, ncount, c.n, c.chk, kTrace ? nullptr : s_push, &s_npush};
   if (threadIdx.x == 0) s_npush = 0u;
 
@@ -624,7 +628,7 @@ __global__ void __launch_bounds__(kBlock, round_kernel_min_blocks<Op>()) k_lb(Tr
 
   const uint64_t p = (uint64_t)gridDim.x * kBlock;
   const uint64_t gt = (uint64_t)blockIdx.x * kBlock + tid;
-  constexpr int U = kULb;
+  constexpr int U = Op::kBatch ? kUMs : kULb;
   unsigned long long lb_edges = 0ull;  // positions this thread processed (cta_stats)
   auto process = [&](const uint64_t (&k)[U], const bool (&ok)[U]) {
     uint32_t ed[U], sv[U], src[U];
