@@ -585,7 +585,8 @@ __global__ void __launch_bounds__(kBlock, round_kernel_min_blocks<Op>()) k_lb(Tr
   const OpArgs a{ca->lab, c.pushed ? c.pushed + (size_t)cur * c.pw : nullptr, r + 1u, ca->k, ca->aux, c.n, c.chk};
   const uint32_t tid = threadIdx.x, lane = tid & 31u;
   // a step of the CTA is kBlock x U positions, at most one push each: the buffer never overflows
-  static_assert(kTrace || kBlock * U <= kPushBuf, "one LB step's pushes must fit the CTA buffer");
+  static_assert(kTrace || kBlock * (Op::kBatch ? kUMs : kULb) <= kPushBuf,
+                "one LB step's pushes must fit the CTA buffer");
   const PushSink sink{Fn, ncount, c.n, c.chk, kTrace ? nullptr : s_push, &s_npush};
   if (threadIdx.x == 0) s_npush = 0u;
 
