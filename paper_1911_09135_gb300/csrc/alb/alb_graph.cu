@@ -392,7 +392,7 @@ alb_status alb_set_app_params(alb_graph g, alb_app app, const alb_params* p) {
   // only the cached work of this application depends on its parameters
   switch (app) {
     case ALB_APP_PAGERANK: free_pagerank(g); break;
-    case ALB_APP_BFS: case ALB_APP_SSSP: free_batch(g); /* fall through */
+    case ALB_APP_BFS: case ALB_APP_SSSP: free_batch(g); [[fallthrough]];
     default: {
       const int internal = app == ALB_APP_BFS ? APP_BFS : app == ALB_APP_SSSP ? APP_SSSP
                          : app == ALB_APP_CC ? APP_CC : APP_KCORE;
