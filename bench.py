@@ -274,8 +274,10 @@ class GpuStep:
             else:
                 units[a] = g.m
             if a == "pr":
+                # set-args, init, output; per iteration the pull and the finalize, and with huge
+                # vertices the hub kernel, the first-level hub sums and the hub finish
                 nh = st["max_hub_count"]
-                launches[a] = 3 + st["rounds"] * (2 + (2 if nh else 0))
+                launches[a] = 3 + st["rounds"] * (2 + (3 if nh else 0))
             else:
                 launches[a] = 2 + st["rounds"] + st["hub_rounds"] + (1 if a == "kcore" else 0)
         return units, launches, stats
