@@ -99,7 +99,7 @@ def load(build_if_missing: bool = False):
     path = lib_path()
     if not os.path.exists(path):
         if not build_if_missing:
-            raise RuntimeError(f"{path} not found; run __graft_entry__.build()")
+            raise RuntimeError(f"{path} not found; build it with paper_1911_09135_gb300._build.build_alb()")
         path = _build.build_alb(checked=os.environ.get("ALB_CHECKED") == "1")
     lib = ctypes.CDLL(path)
     S = ctypes.c_int

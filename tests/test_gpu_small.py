@@ -545,7 +545,7 @@ def test_tile_push_overflow_goes_to_the_frontier():
         G.bfs(0, o)
         assert np.array_equal(host(o), oracle.bfs(g.n, g.offsets, g.indices, 0)), t
         if t == 1 << 40:
-            assert G.stats()["pushes"] > 3 * 2048  # round 1 pushes the three stars' leaves
+            assert G.stats()["pushes"] > 3 * 2048  # the first BFS levels hold the three stars' leaves
         G.sssp(0, o)
         assert np.array_equal(host(o), oracle.sssp(g.n, g.offsets, g.indices, g.weights, 0)), t
         G.cc(o)
