@@ -89,7 +89,8 @@ typedef struct {
   int64_t hub_threshold;
   uint32_t twc_warp_min;   /* degree >= this goes to the warp bin (default 32) */
   uint32_t twc_cta_min;    /* degree >= this goes to the CTA bin (default 256, the CTA size) */
-  uint32_t grid_blocks;    /* CTAs of every round kernel; 0 = SMs x resident CTAs per SM */
+  uint32_t grid_blocks;    /* CTAs of every round kernel; 0 = SMs x resident CTAs per SM of each kernel
+                            * (PageRank's pull kernel: 8 such waves) */
   uint32_t distribution;   /* LB edge distribution: 0 cyclic (default), 1 blocked (Sec. 4.1) */
   uint32_t exec_mode;      /* 0: device-side round loop in a CUDA graph (default); 1: host loop */
   uint32_t max_rounds;     /* 0: n + 1 (enough for every app); ALB_ERR_TIMEOUT when reached */
