@@ -78,24 +78,32 @@ def parse_args():
     return ap.parse_args()
 
 
+def _gen_threads() -> int:
+    """Generator threads for this process: its share of the host's cores when torchrun starts
+    several ranks on one node (the output does not depend on the thread count)."""
+    local = int(os.environ.get("LOCAL_WORLD_SIZE", "1"))
+    return max(1, len(os.sched_getaffinity(0)) // max(1, local))
+
+
 def workload(name):
     from paper_1911_09135_gb300 import graphgen as gg
+    nt = _gen_threads()
     if name == "rmat24-hubs":
-        g = gg.rmat24_hubs_sym()
+        g = gg.rmat24_hubs_sym(nthreads=nt)
         desc = ("RMAT(a=.57,b=.19,c=.19) scale 24, edge factor 16, seed 3, + 16 hubs x 2^22 "
                 "uniform targets, symmetrised, dedup, weights U[1,100]")
         apps = APPS
     elif name == "rmat22-hubs":
-        g = gg.scaled_hub_graph(22)
+        g = gg.scaled_hub_graph(22, nthreads=nt)
         desc = ("RMAT scale 22, edge factor 16, seed 3, + 16 hubs x 2^20 uniform targets, "
                 "symmetrised, dedup, weights U[1,100] (small member of the severe-imbalance family)")
         apps = APPS
     elif name == "rmat22":
-        g = gg.rmat22_sym()
+        g = gg.rmat22_sym(nthreads=nt)
         desc = "RMAT scale 22, edge factor 16, seed 2, symmetrised, dedup, weights U[1,100]"
         apps = ("bfs", "sssp")
     else:
-        g = gg.rmat16_directed()
+        g = gg.rmat16_directed(nthreads=nt)
         desc = "RMAT scale 16, edge factor 16, seed 1, directed, dedup"
         apps = ("bfs",)
     return g, desc, apps
