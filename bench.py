@@ -75,6 +75,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-roofline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--small-sms", type=int, default=0,
+                    help="serve: an SM partition of this many SMs for the small graphs (0 = none)")
+    ap.add_argument("--big-slots", type=int, default=2, help="serve: slots per large graph")
     return ap.parse_args()
 
 
@@ -733,7 +736,7 @@ def serve_arm(args, dist):
     alb.load()
     scales = (14, 15, 17, 18, 20, 21, 23, 24)
     graphs = [gg.rmat(sc, 16 << sc, 500 + i, symmetrize=True, weighted=True) for i, sc in enumerate(scales)]
-    srv = serve.Server(graphs, tune=True)
+    srv = serve.Server(graphs, tune=True, small_sms=args.small_sms, big_slots=args.big_slots)
     reqs = serve.poisson_requests(graphs, 20000, rate=2000.0, seed=5)
     # warm every slot's cached graphs once
     warm = [serve.Request(-1 - 3 * i - j, 0.0, i, k, int(np.argmax(graphs[i].degrees())))
@@ -769,6 +772,8 @@ def serve_arm(args, dist):
                            "speedup": round(t_plain / t_batched, 2)},
             "config": {"workload": "8 resident RMAT graphs, scales 14-24 (14,15,17,18,20,21,23,24), "
                                    "seeds 500+i, symmetrised, w in [1,100]; Poisson 2000/s, seed 5",
+                       "hardware_queues": int(os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS", "8")),
+                       "small_sms": args.small_sms, "big_slots": args.big_slots,
                        "graphs_m": [g.m for g in graphs], "knobs": "autotuned per graph and app"}}
     if dist.rank == 0:
         print(json.dumps(line), flush=True)
