@@ -54,6 +54,55 @@ KERNEL_SOURCES = {
 }
 
 
+UNITS_DESC = ("traversed edges (CSR entries), the same definition for the GPU path and the "
+              "oracle: bfs and sssp = degree sum of the reached vertices (Graph500 style); "
+              "cc = m (every entry is examined at least once; label propagation's repeat "
+              "visits are not counted); kcore = degree sum of the peeled vertices (the entries "
+              "peeling examines); pr = m x iterations")
+
+
+def unit_counts(g, out: dict, pr_iters: int) -> dict:
+    """Units of one step of each app from its results (numpy arrays): see UNITS_DESC."""
+    deg = g.degrees().astype(np.int64)
+    u = {}
+    for a, r in out.items():
+        if a in ("bfs", "sssp"):
+            u[a] = int(deg[np.asarray(r).view(np.uint32) != INF].sum())
+        elif a == "cc":
+            u[a] = int(g.m)
+        elif a == "kcore":
+            u[a] = int(deg[np.asarray(r).view(np.uint32) == 0].sum())
+        elif a == "pr":
+            u[a] = int(g.m) * int(pr_iters)
+    return u
+
+
+def step_config(g, desc, apps, src, world) -> dict:
+    """The workload of one step, identical in the GPU arm and the reference (oracle) arm."""
+    return {"workload": f"{g.name}: {desc}", "n": g.n, "m": g.m, "apps": list(apps),
+            "source": int(src), "kcore_k": KCORE_K, "pagerank": {"d": PR_D, "tol": PR_TOL},
+            "l2": l2_note(g),
+            "parallelism": f"replicas x{world} (the path does not shard)", "units": UNITS_DESC}
+
+
+def l2_note(g) -> str:
+    csr = 4 * (g.n + 1) + 4 * g.m * (2 if g.weights is not None else 1)
+    if csr > (129 << 20):
+        return f"no flush: the CSR ({csr / 1e9:.2f} GB) is larger than L2 (129 MB)"
+    return f"no flush: the CSR ({csr / 1e6:.1f} MB) fits L2; a launch-bound configuration"
+
+
+def tune_source(g, src: int) -> int:
+    """A vertex other than the timed source for the autotuner's bfs/sssp trials (seeded draw
+    among the non-isolated vertices), so the knobs are not fitted to the timed query."""
+    cand = np.nonzero(g.degrees() > 0)[0]
+    cand = cand[cand != src]
+    if cand.size == 0:
+        return int(src)
+    rng = np.random.Generator(np.random.Philox(key=7))
+    return int(cand[rng.integers(0, cand.size)])
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -210,6 +259,30 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+class TimedRegion:
+    """Barrier + device synchronisation on both sides and nvidia-smi clock samples throughout
+    (the clocks record of a bench line)."""
+
+    def __init__(self, dist):
+        self.dist = dist
+        self.sampler = ClockSampler(dist.local)
+        self.clocks = None
+
+    def __enter__(self):
+        import torch
+        self.dist.barrier()
+        torch.cuda.synchronize()
+        self.sampler.start()
+        return self
+
+    def __exit__(self, *exc):
+        import torch
+        torch.cuda.synchronize()
+        self.dist.barrier()
+        self.clocks = self.sampler.stop()
+        return False
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def measured_peaks():
@@ -271,19 +344,15 @@ class GpuStep:
     def calibrate(self):
         """One untimed pass: traversed-edge units and kernel launches per app."""
         g = self.g
-        deg = g.degrees().astype(np.int64)
-        units, launches, stats = {}, {}, {}
+        launches, stats, outs = {}, {}, {}
+        pr_iters = 0
         for a in self.apps:
             self.run_app(a)
             st = self.G.stats()
             stats[a] = st
-            if a in ("bfs", "sssp"):
-                reached = self.out[a].cpu().numpy().view(np.uint32) != INF
-                units[a] = int(deg[reached].sum())  # edges of reached vertices
-            elif a == "pr":
-                units[a] = g.m * int(self.iters.item())
-            else:
-                units[a] = g.m
+            outs[a] = self.out[a].cpu().numpy()
+            if a == "pr":
+                pr_iters = int(self.iters.item())
             if a == "pr":
                 # set-args, init, output; per iteration the pull and the finalize, and with huge
                 # vertices the hub kernel, the first-level hub sums and the hub finish
@@ -291,7 +360,7 @@ class GpuStep:
                 launches[a] = 3 + st["rounds"] * (2 + (3 if nh else 0))
             else:
                 launches[a] = 2 + st["rounds"] + st["hub_rounds"] + (1 if a == "kcore" else 0)
-        return units, launches, stats
+        return unit_counts(g, outs, pr_iters), launches, stats
 
     def roofline_pass(self):
         """Each app once more in the host-loop mode with every kernel timed by CUDA events."""
@@ -346,9 +415,10 @@ def gpu_arm(args, dist):
             paper_rule_ms[a] = round(e0.elapsed_time(e1) / 2, 3)
     # autotuned knobs per app (outside the timed region; results do not depend on them)
     tuned = {}
+    tsrc = tune_source(g, step.src)
     if not args.no_tune:
         for a in apps:
-            p, _ = step.G.autotune(a, step.src, reps=2)
+            p, _ = step.G.autotune(a, tsrc, reps=2)
             tuned[a] = {"hub_threshold": p.hub_threshold, "twc_cta_min": p.twc_cta_min,
                         "twc_warp_min": p.twc_warp_min}
     if args.exec_mode == "host":
@@ -418,17 +488,33 @@ def gpu_arm(args, dist):
     if not args.no_e2e:
         e2e = e2e_measure(args, g, apps, alb, torch, units_step, dist, tuned)
 
+    # the last timed step's PageRank vector, for its distance to the FP64 oracle (below)
+    pr_gpu = step.out["pr"].cpu().numpy().astype(np.float64) if "pr" in apps else None
     step.close()
+    pr_oracle = None
+    if dist.rank == 0 and pr_gpu is not None:
+        # FP64 oracle on the same graph, outside every timed region, on all host cores
+        import oracle
+        cores = len(os.sched_getaffinity(0))
+        t_or = time.perf_counter()
+        x_ref, it_ref, _ = oracle.pagerank(g.n, g.offsets, g.indices, PR_D, PR_TOL, PR_MAX,
+                                           assume_symmetric=g.symmetric, nthreads=cores)
+        pr_oracle = {"l1_vs_oracle": float(np.abs(pr_gpu - x_ref).sum()), "oracle_iterations": it_ref,
+                     "oracle_s": round(time.perf_counter() - t_or, 1), "oracle_cores": cores}
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(g, apps, budget_s=20.0)
+        cpu = cpu_baseline(g, apps, step.src, units)
 
     per_app = {a: {"gteps": round(units[a] / (app_ms[a] * 1e-3) / 1e9, 3),
                    "ms": round(app_ms[a], 3), "units": units[a],
+                   "edges_examined": int(cal_stats[a]["edges_twc"] + cal_stats[a]["edges_lb"]),
                    "rounds": cal_stats[a]["rounds"], "hub_rounds": cal_stats[a]["hub_rounds"]}
                for a in apps}
     if "pr" in apps:
         per_app["pr"]["l1_last_change"] = cal_stats["pr"]["pr_l1"]
+        if pr_oracle:
+            per_app["pr"].update(pr_oracle)
+            per_app["pr"]["l1_bound"] = 1e-5
     if paper_rule_ms:
         for a in apps:
             per_app[a]["ms_paper_rule_threshold"] = paper_rule_ms[a]
@@ -437,18 +523,15 @@ def gpu_arm(args, dist):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32 (integer apps), f32 (pagerank)", "data": "synthetic",
-        "config": {"workload": f"{g.name}: {desc}", "n": g.n, "m": g.m, "apps": list(apps),
-                   "exec_mode": args.exec_mode, "source": int(step.src), "kcore_k": KCORE_K,
-                   "pagerank": {"d": PR_D, "tol": PR_TOL},
-                   "knobs": ("autotuned per app by alb_autotune before timing" if tuned
-                             else "paper's rule: threshold = threads of the LB kernel"),
-                   "tuned": tuned or None,
-                   "hub_threshold": {a: cal_stats[a]["hub_threshold"] for a in apps},
-                   "lb_threads": cal_stats[apps[0]]["lb_threads"],
-                   "l2": "no flush: the CSR (>= 5 GB) is larger than L2 (129 MB)",
-                   "parallelism": f"replicas x{dist.world} (the path does not shard)",
-                   "units": "traversed edges: bfs/sssp = degree sum of reached vertices, "
-                            "cc/kcore = m, pr = m x iterations"},
+        "config": step_config(g, desc, apps, step.src, dist.world),
+        "run": {"exec_mode": args.exec_mode,
+                "knobs": ("autotuned per app by alb_autotune before timing, on a source other "
+                          "than the timed one" if tuned
+                          else "paper's rule: threshold = threads of the LB kernel"),
+                "tune_source": int(tsrc) if tuned else None,
+                "tuned": tuned or None,
+                "hub_threshold": {a: cal_stats[a]["hub_threshold"] for a in apps},
+                "lb_threads": cal_stats[apps[0]]["lb_threads"]},
         "per_app": per_app,
         "gpu_launches": int(sum(launches.values()) * args.steps),
         "roofline": roof,
@@ -508,67 +591,104 @@ def e2e_measure(args, g, apps, alb, torch, units_step, dist, tuned=None):
 
 # ------------------------------------------------------------------ CPU oracle (baseline)
 
-def oracle_sample(g, apps, budget_s):
-    """Run the oracle's apps on the workload graph, in a fixed order, until the time budget is
-    spent; PageRank contributes single iterations. Returns (units, seconds, what ran)."""
+def oracle_app(g, a, src):
+    """One application of the step by the serial CPU oracle, on the full workload graph.
+    PageRank runs ONE iteration (its rate per iteration); the others run to completion.
+    Returns (result or None, units processed, seconds)."""
     import oracle
-    deg = g.degrees().astype(np.int64)
-    src = g.max_degree_vertex()
-    ran, units = [], 0
     t0 = time.perf_counter()
-    order = [a for a in ("bfs", "cc", "kcore", "pr", "sssp") if a in apps]
-    for a in order:
-        if ran and time.perf_counter() - t0 > budget_s:
-            break
-        if a == "bfs":
-            lv = oracle.bfs(g.n, g.offsets, g.indices, src)
-            units += int(deg[lv != INF].sum())
-        elif a == "cc":
-            oracle.cc(g.n, g.offsets, g.indices)
-            units += g.m
-        elif a == "kcore":
-            oracle.kcore(g.n, g.offsets, g.indices, KCORE_K)
-            units += g.m
-        elif a == "pr":
-            oracle.pagerank(g.n, g.offsets, g.indices, PR_D, PR_TOL, 1, assume_symmetric=True,
-                            nthreads=1)
-            units += g.m
-            a = "pr(1 iteration)"
-        elif a == "sssp":
-            d = oracle.sssp(g.n, g.offsets, g.indices, g.weights, src)
-            units += int(deg[d != INF].sum())
-        ran.append(a)
-    return units, time.perf_counter() - t0, ran
+    if a == "bfs":
+        r = oracle.bfs(g.n, g.offsets, g.indices, src)
+    elif a == "sssp":
+        r = oracle.sssp(g.n, g.offsets, g.indices, g.weights, src)
+    elif a == "cc":
+        r = oracle.cc(g.n, g.offsets, g.indices)
+    elif a == "kcore":
+        r = oracle.kcore(g.n, g.offsets, g.indices, KCORE_K)
+    else:
+        oracle.pagerank(g.n, g.offsets, g.indices, PR_D, PR_TOL, 1, assume_symmetric=g.symmetric,
+                        nthreads=1)
+        return None, int(g.m), time.perf_counter() - t0
+    sec = time.perf_counter() - t0
+    return r, unit_counts(g, {a: r}, 0)[a], sec
 
 
-def cpu_baseline(g, apps, budget_s):
-    units, sec, ran = oracle_sample(g, apps, budget_s)
-    return {"value": round(units / sec / 1e9, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{' + '.join(ran)} on the full workload graph, serial CPU oracle, "
-                      f"{sec:.1f} s; host has {len(os.sched_getaffinity(0))} cores"}
+def mix_rate(step_units: dict, samples: dict) -> float:
+    """Throughput (units/s) of the oracle on one step's unit mix: each app's time is its
+    measured rate applied to that app's units in the step (PageRank: per-iteration rate times
+    the step's iterations). samples[a] = list of (units, seconds)."""
+    t = 0.0
+    for a, u in step_units.items():
+        su = sum(x for x, _ in samples[a])
+        ss = sum(y for _, y in samples[a])
+        t += u * ss / su if su else 0.0
+    return sum(step_units.values()) / t
+
+
+def cpu_baseline(g, apps, src, step_units):
+    """Every app of the step once by the serial oracle (PageRank: one iteration), weighted by the
+    GPU step's unit mix."""
+    samples = {a: [oracle_app(g, a, src)[1:]] for a in apps}
+    sec = sum(s for v in samples.values() for _, s in v)
+    return {"value": round(mix_rate(step_units, samples) / 1e9, 4), "unit": UNIT, "cores": 1,
+            "kind": "oracle",
+            "sample": (f"{' + '.join(a if a != 'pr' else 'pr (1 iteration)' for a in apps)} once each "
+                       f"on the full workload graph by the serial CPU oracle ({sec:.1f} s), "
+                       f"weighted by the step's units per app; host has "
+                       f"{len(os.sched_getaffinity(0))} cores")}
 
 
 def reference_arm(args, dist):
+    """The CPU oracle as it stands on the GPU arm's workload, config, metric and units. A step
+    is one application of the five-app mix in turn (bfs, sssp, cc, pr, kcore; PageRank as one
+    iteration), run to completion on the full graph; the value is the oracle's throughput on the
+    whole step's unit mix (each app's measured rate applied to its units in the step; PageRank's
+    iterations are the oracle's own count at tol 1e-6, found once before timing on all cores)."""
     if dist.rank != 0:
         return
     g, desc, apps = workload(args.workload)
+    src = g.max_degree_vertex()
+    import oracle
+    # untimed: PageRank's iteration count at the step's tolerance (the other apps' units come
+    # from their first timed result)
+    step_units = {}
+    pr_iters = 0
+    if "pr" in apps:
+        _, pr_iters, _ = oracle.pagerank(g.n, g.offsets, g.indices, PR_D, PR_TOL, PR_MAX,
+                                         assume_symmetric=g.symmetric,
+                                         nthreads=len(os.sched_getaffinity(0)))
+        step_units["pr"] = int(g.m) * pr_iters
+    cheap = min(apps, key=lambda a: {"kcore": 0, "bfs": 1, "cc": 2, "pr": 3, "sssp": 4}[a])
     for _ in range(max(args.warmup, 0)):
-        oracle_sample(g, apps, budget_s=3.0)
-    tot_u, tot_s, ran = 0, 0.0, []
-    for _ in range(args.steps):
-        u, s, ran = oracle_sample(g, apps, budget_s=3.0)
-        tot_u += u
-        tot_s += s
-    value = tot_u / tot_s / 1e9
+        oracle_app(g, cheap, src)
+    order = list(apps)
+    plan = [order[i % len(order)] for i in range(max(args.steps, len(order)))]
+    samples = {a: [] for a in apps}
+    tot_s = 0.0
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        for i in range(k, len(plan), args.steps):  # every app at least once over the K steps
+            r, u, sec = oracle_app(g, plan[i], src)
+            samples[plan[i]].append((u, sec))
+            if plan[i] not in step_units:
+                step_units[plan[i]] = u
+        tot_s += time.perf_counter() - t0
+    step_units = {a: step_units[a] for a in apps}
+    value = mix_rate(step_units, samples) / 1e9
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": dist.world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * tot_s / args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32 (integer apps), f64 (pagerank)", "data": "synthetic", "impl": "reference",
-        "config": {"workload": f"{g.name}: {desc}", "n": g.n, "m": g.m, "apps": list(apps)},
+        "config": step_config(g, desc, apps, src, dist.world),
+        "per_app": {a: {"units": step_units[a], "samples": len(samples[a]),
+                        "gteps": round(sum(x for x, _ in samples[a]) / sum(y for _, y in samples[a]) / 1e9, 4)}
+                    for a in apps},
         "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"each step: {' + '.join(ran)} (serial CPU oracle) on the full "
-                                   f"workload graph"},
+                         "sample": ("each step: the next app of the five-app mix (PageRank as one "
+                                    "iteration) by the serial CPU oracle on the full workload graph"
+                                    + (f"; pagerank iterations {pr_iters} (the oracle's own count)"
+                                       if "pr" in apps else ""))},
         "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -606,29 +726,34 @@ def batch_arm(args, dist):
         return e0.elapsed_time(e1) / reps
 
     res = {}
+    region = TimedRegion(dist)
+    region.__enter__()
     if args.workload == "batch-sources":
         g = gg.rmat22_sym()
         rng = np.random.Generator(np.random.Philox(key=4))
         srcs = rng.integers(0, g.n, size=128).astype(np.uint32)
         d_srcs = dev(srcs)
+        # the knobs are chosen on other queries than the timed ones (seed 40)
+        tsrcs = np.random.Generator(np.random.Philox(key=40)).integers(0, g.n, size=128).astype(np.uint32)
+        d_tsrcs = dev(tsrcs)
         G = alb.Graph(g.n, dev(g.offsets), dev(g.indices), dev(g.weights), symmetric=True)
         out = torch.empty(128 * g.n, dtype=torch.int32, device="cuda")
         n = g.n
         for app, single, batch in (("bfs", alb.alb_bfs, alb.alb_bfs_batch),
                                    ("sssp", alb.alb_sssp, alb.alb_sssp_batch)):
-            tuned, _ = G.autotune(app, int(srcs[0]), reps=2)  # the plain path's knobs
+            tuned, _ = G.autotune(app, tune_source(g, int(srcs[0])), reps=2)  # the plain path's knobs
             def plain():
                 for i, s in enumerate(srcs.tolist()):
                     single(G.h, s, out[i * n:(i + 1) * n])
             ms_plain = timed(plain, max(1, args.steps // 2))
             # the batched path gets its own threshold (multi-source rounds relax every active
             # source of an edge, so the best split between TWC and the LB kernel can differ),
-            # chosen by timing the batch itself; the TWC cut-offs stay the tuned ones
+            # chosen by timing a batch of 128 other sources; the TWC cut-offs stay the tuned ones
             cand = sorted({int(tuned.hub_threshold), -1, 1 << 12, 1 << 14, 1 << 16, 1 << 18})
             trial = {}
             for t in cand:
                 G.set_app_params(app, hub_threshold=t)
-                trial[t] = timed(lambda: batch(G.h, d_srcs, 128, out), 1)
+                trial[t] = timed(lambda: batch(G.h, d_tsrcs, 128, out), 1)
             t_best = min(trial, key=trial.get)
             G.set_app_params(app, hub_threshold=t_best)
             ms_batch = timed(lambda: batch(G.h, d_srcs, 128, out), args.steps)
@@ -665,12 +790,16 @@ def batch_arm(args, dist):
         U.close()
         desc = (f"512 RMAT graphs, samples log-uniform in [2^10, 2^22] (seed 4), symmetrised, "
                 f"w in [1,100]; union n={u.n} m={u.m}; source 0 of each")
+    region.__exit__(None, None, None)
     q = sum(r["queries"] for r in res.values())
     t = sum(r["ms_batched"] for r in res.values())
     tp = sum(r["ms_plain"] for r in res.values())
     line = {"metric": "batched throughput vs one-query-at-a-time plain path (bfs + sssp)",
             "value": round(q / (t * 1e-3), 1), "unit": "queries/s", "n_gpus": dist.world,
-            "steps": args.steps, "higher_is_better": True, "speedup_vs_plain": round(tp / t, 2),
+            "steps": args.steps, "warmup": 1, "ms_per_step": round(t, 3),
+            "step": "one batched call per app (bfs, then sssp) over all the queries",
+            "higher_is_better": True, "speedup_vs_plain": round(tp / t, 2),
+            "clocks": region.clocks,
             "config": {"workload": args.workload + ": " + desc}, "per_app": res}
     if dist.rank == 0:
         print(json.dumps(line), flush=True)
@@ -697,6 +826,8 @@ def ablation_arm(args, dist):
     settings += [(f"t=2^{k}", {"hub_threshold": 1 << k}) for k in (8, 10, 12, 14, 16, 18, 20)]
     base = step.G.params()
     table = {}
+    region = TimedRegion(dist)
+    region.__enter__()
     for name, kw in settings:
         step.G.set_params(**{**{"hub_threshold": base.hub_threshold, "distribution": 0}, **kw})
         row = {}
@@ -713,9 +844,13 @@ def ablation_arm(args, dist):
             st = step.G.stats()
             row[a] = {"ms": round(e0.elapsed_time(e1) / args.steps, 3), "lb_rounds": st["hub_rounds"]}
         table[name] = row
+    region.__exit__(None, None, None)
     step.close()
+    ms_all = sum(r["ms"] for row in table.values() for r in row.values())
     line = {"metric": "per-app device time (ms) by load-balancing policy", "unit": "ms",
-            "higher_is_better": False, "n_gpus": dist.world, "steps": args.steps,
+            "higher_is_better": False, "n_gpus": dist.world, "steps": args.steps, "warmup": 1,
+            "ms_per_step": round(ms_all, 3),
+            "step": "one call of every app under every policy", "clocks": region.clocks,
             "config": {"workload": f"{g.name}: {desc}",
                        "default_threshold": "threads of the LB kernel (alb_params.hub_threshold = -1)"},
             "table": table}
@@ -743,7 +878,9 @@ def serve_arm(args, dist):
             for i in range(len(graphs)) for j, k in enumerate(serve.KINDS)]
     srv.run(warm, realtime=False)
     e0 = srv.edges
-    wall = srv.run(reqs, realtime=True, timeout=900)
+    region = TimedRegion(dist)
+    with region:
+        wall = srv.run(reqs, realtime=True, timeout=900)
     lat = serve.latency_stats(reqs)
     per_graph = serve.slot_stats(srv, reqs)
     gteps = (srv.edges - e0) / wall / 1e9
@@ -764,6 +901,8 @@ def serve_arm(args, dist):
     srv.close()
     line = {"metric": "served bfs/sssp/cc requests: p50/p99 latency and throughput", "unit": "queries/s",
             "value": round(len(reqs) / wall, 1), "higher_is_better": True, "n_gpus": dist.world,
+            "steps": 1, "warmup": 1, "ms_per_step": round(wall * 1e3, 1),
+            "step": "the whole open-loop run of the Poisson requests", "clocks": region.clocks,
             "latency": lat, "gteps": round(gteps, 3), "offered_rate": 2000.0, "requests": len(reqs),
             "wall_s": round(wall, 3), "deferred_admissions": srv.deferred, "per_graph": per_graph,
             "below_saturation": below,

@@ -31,9 +31,11 @@
  *   - Calls on one alb_graph must be ordered (same stream, or externally
  *     synchronised): a handle owns one workspace and is not thread-safe.
  *     Different handles are independent. The first call of each kind on a
- *     handle allocates its workspace and instantiates a CUDA graph, which can
- *     wait for the whole device: make it (warm the handle) before running
- *     several handles concurrently on different streams.
+ *     handle allocates its workspace and instantiates a CUDA graph; it first
+ *     waits for the whole device to be idle (cudaDeviceSynchronize), so no
+ *     set-up ever overlaps running kernels. Make those first calls (warm the
+ *     handle) before running several handles concurrently on different streams,
+ *     or the other streams stall while one handle sets up.
  *   - Argument errors are returned synchronously and enqueue nothing. Errors
  *     detected on the device (round limit exceeded, corrupt CSR) are latched in
  *     the handle and returned by alb_sync() and alb_get_stats().
@@ -277,9 +279,12 @@ uint32_t alb_threshold_rule(uint32_t num_sms, uint32_t threads_per_sm);
  * library until the process exits.
  *   n <= ALB_NOALLOC_MAX_VERTICES, else ALB_ERR_INVALID_ARG (nothing enqueued);
  *   d_offsets[n+1], d_indices[m], d_levels[n] must be device memory.
- * The CSR is checked on the device first (ALB_ERR_INVALID_ARG if offsets[0] != 0
- * or offsets[n] != m, ALB_ERR_DEVICE if an index is >= n). The call synchronises
- * `stream` once per round and returns after d_levels is complete.
+ * The CSR is checked on the device first: ALB_ERR_INVALID_ARG if offsets[0] != 0,
+ * offsets[n] != m or the offsets decrease anywhere; ALB_ERR_DEVICE if an index is
+ * >= n. Nothing is traversed after a failed check. In the bounds-checked build
+ * (libalb_checked.so) an access the round kernels had to skip is reported as
+ * ALB_ERR_DEVICE at the end of the call. The call synchronises `stream` once per
+ * round and returns after d_levels is complete.
  * The first call on a device looks up the array's device address; make that
  * first call before any stream capture begins. Every call on a device shares
  * the one array and overwrites it, so calls whose work overlaps on the GPU

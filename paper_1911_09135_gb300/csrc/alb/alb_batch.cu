@@ -292,6 +292,8 @@ static alb_status ensure_batch(alb_graph g, bool group_arrays, uint32_t nsrc, cu
   if (!b) return ALB_ERR_OOM;
   const size_t n = g->n;
   if (group_arrays && !b->lab) {
+    alb_status rc = setup_barrier();
+    if (rc != ALB_OK) return rc;
     ALB_CUDA_TRY(cudaMalloc((void**)&b->lab, sizeof(uint32_t) * n * 32u));
     ALB_CUDA_TRY(cudaMalloc((void**)&b->seen, sizeof(uint32_t) * n));
     ALB_CUDA_TRY(cudaMalloc((void**)&b->act, sizeof(unsigned long long) * n * 2u));
@@ -305,6 +307,8 @@ static alb_status ensure_batch(alb_graph g, bool group_arrays, uint32_t nsrc, cu
     // Stream-ordered: work already queued on s (an earlier batch's seed kernel) may still read
     // the old buffer, and a plain cudaFree need not wait for it.
     const uint32_t cap = nsrc < 1024u ? 1024u : nsrc;
+    alb_status rc = setup_barrier();
+    if (rc != ALB_OK) return rc;
     if (b->srcs) ALB_CUDA_TRY(cudaFreeAsync(b->srcs, s));
     b->srcs = nullptr;
     ALB_CUDA_TRY(cudaMallocAsync((void**)&b->srcs, sizeof(uint32_t) * cap, s));
@@ -475,7 +479,8 @@ static alb_status run_groups(alb_graph g, BatchKind kind, const uint32_t* hd_src
   if (rc != ALB_OK) return rc;
   BatchWs* b = g->batch;
   if ((rc = stage_srcs(g, hd_srcs, k, s)) != ALB_OK) return rc;
-  if (!b->exec[kind] && (rc = build_batch_graph(g, kind)) != ALB_OK) return rc;
+  if (!b->exec[kind] && ((rc = setup_barrier()) != ALB_OK || (rc = build_batch_graph(g, kind)) != ALB_OK))
+    return rc;
   const bool dev = is_device_ptr(out);
   const size_t n = g->n;
   const uint32_t ngroups = (k + 31u) / 32u;
@@ -505,7 +510,10 @@ static alb_status run_groups(alb_graph g, BatchKind kind, const uint32_t* hd_src
     g->last_kind = 0;
     return ALB_OK;
   }
-  if (!dev && !b->tmp) ALB_CUDA_TRY(cudaMalloc((void**)&b->tmp, sizeof(uint32_t) * (size_t)g->n * 32u));
+  if (!dev && !b->tmp) {
+    if ((rc = setup_barrier()) != ALB_OK) return rc;
+    ALB_CUDA_TRY(cudaMalloc((void**)&b->tmp, sizeof(uint32_t) * (size_t)g->n * 32u));
+  }
   for (uint32_t g0 = 0; g0 < k; g0 += 32u) {
     const uint32_t ns = (k - g0) < 32u ? (k - g0) : 32u;
     uint32_t* dst = dev ? out + (size_t)g0 * n : b->tmp;
@@ -528,7 +536,8 @@ static alb_status run_multi(alb_graph g, BatchKind kind, const uint32_t* hd_srcs
   if (rc != ALB_OK) return rc;
   BatchWs* b = g->batch;
   if ((rc = stage_srcs(g, hd_srcs, k, s)) != ALB_OK) return rc;
-  if (!b->exec[kind] && (rc = build_batch_graph(g, kind)) != ALB_OK) return rc;
+  if (!b->exec[kind] && ((rc = setup_barrier()) != ALB_OK || (rc = build_batch_graph(g, kind)) != ALB_OK))
+    return rc;
   const bool dev = is_device_ptr(out);
   uint32_t* lab = out;
   if (!dev) {

@@ -17,8 +17,17 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+alb_status setup_barrier() {
+  ALB_CUDA_TRY(cudaDeviceSynchronize());
+  return ALB_OK;
+}
+
 alb_status ensure_tmp(alb_graph g) {
-  if (!g->tmp) ALB_CUDA_TRY(cudaMalloc((void**)&g->tmp, sizeof(uint32_t) * (size_t)g->n));
+  if (!g->tmp) {
+    alb_status rc = setup_barrier();
+    if (rc != ALB_OK) return rc;
+    ALB_CUDA_TRY(cudaMalloc((void**)&g->tmp, sizeof(uint32_t) * (size_t)g->n));
+  }
   return ALB_OK;
 }
 
@@ -66,7 +75,7 @@ __global__ void k_scan_graph(const uint32_t* off, const uint32_t* idx, const uin
 }
 
 static void free_graph_memory(alb_graph g) {
-  if (!g->csr_refs || --(*g->csr_refs) == 0) {
+  if (!g->csr_refs || g->csr_refs->fetch_sub(1) == 1) {
     cudaFree(g->off);
     cudaFree(g->idx);
     cudaFree(g->w);
@@ -278,7 +287,7 @@ alb_status alb_graph_create(uint32_t n, uint64_t m, const uint32_t* hd_offsets,
   g->has_w = hd_weights != nullptr || m == 0;  // a graph without edges has nothing to weigh
   const size_t nb = sizeof(uint32_t) * (size_t)n;
   const size_t mb = sizeof(uint32_t) * (size_t)(m ? m : 1);
-  g->csr_refs = new (std::nothrow) int(1);
+  g->csr_refs = new (std::nothrow) std::atomic<int>(1);
   if (!g->csr_refs) return fail(ALB_ERR_OOM);
   cudaError_t e = cudaSuccess;
   e = cudaMalloc((void**)&g->off, nb + sizeof(uint32_t));
@@ -340,7 +349,7 @@ alb_status alb_graph_clone(alb_graph src, alb_graph* out) {
   g->idx = src->idx;
   g->w = src->w;
   g->csr_refs = src->csr_refs;
-  ++(*g->csr_refs);
+  g->csr_refs->fetch_add(1);
   g->num_sms = src->num_sms;
   for (int a = 0; a < 5; ++a) g->cfg[a] = src->cfg[a];
   select_cfg(g, ALB_APP_BFS);

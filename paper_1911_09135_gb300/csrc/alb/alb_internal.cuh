@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -111,7 +112,7 @@ struct alb_graph_s {
   uint32_t* off = nullptr;
   uint32_t* idx = nullptr;
   uint32_t* w = nullptr;
-  int* csr_refs = nullptr;  // handles sharing off/idx/w (alb_graph_clone); the last one frees them
+  std::atomic<int>* csr_refs = nullptr;  // handles sharing off/idx/w (alb_graph_clone); the last frees them
 
   // per-application launch configuration (indexed by alb_app); the fields below hold the
   // configuration of the application being called (select_cfg copies it in)
@@ -170,6 +171,10 @@ namespace alb {
   } while (0)
 
 bool is_device_ptr(const void* p);
+// Set-up (a device allocation, a CUDA-graph instantiation, PageRank's per-graph inspection) runs
+// with the device idle: this waits for all work on the device. A handle's first call of each kind
+// calls it once, so no set-up ever overlaps kernels of other handles or streams.
+alb_status setup_barrier();
 alb_status ensure_tmp(alb_graph g);
 alb_status traversal_status(alb_graph g);   // reads h_st after a sync
 alb_status free_traversal_graphs(alb_graph g);

@@ -734,6 +734,10 @@ static alb_status pr_grids(alb_graph g, uint32_t* pull, uint32_t* hub) {
 // One-time setup per graph and parameters: bins, hub prefix, buffers.
 static alb_status pr_setup(alb_graph g, cudaStream_t s) {
   if (g->pr && g->pr->ready) return ALB_OK;
+  {
+    alb_status rb = setup_barrier();
+    if (rb != ALB_OK) return rb;
+  }
   if (!g->pr) g->pr = new (std::nothrow) PrWs();
   PrWs* w = g->pr;
   if (!w) return ALB_ERR_OOM;
@@ -984,7 +988,10 @@ extern "C" alb_status alb_pagerank(alb_graph g, float damping, double tol, uint3
   const bool dev_rank = is_device_ptr(hd_rank);
   float* rank = hd_rank;
   if (!dev_rank) {
-    if (!w->tmp_rank) ALB_CUDA_TRY(cudaMalloc((void**)&w->tmp_rank, sizeof(float) * (size_t)g->n));
+    if (!w->tmp_rank) {
+      if ((rc = setup_barrier()) != ALB_OK) return rc;
+      ALB_CUDA_TRY(cudaMalloc((void**)&w->tmp_rank, sizeof(float) * (size_t)g->n));
+    }
     rank = w->tmp_rank;
   }
   const bool dev_l1 = hd_l1 && is_device_ptr(hd_l1);
@@ -999,7 +1006,8 @@ extern "C" alb_status alb_pagerank(alb_graph g, float damping, double tol, uint3
     k_pr_output<<<g->blocks, kBlock, 0, s>>>(c);
   } else if (g->params.exec_mode == 0) {
     if (!w->exec) {
-      rc = pr_build_graph(g);
+      rc = setup_barrier();
+      if (rc == ALB_OK) rc = pr_build_graph(g);
       if (rc != ALB_OK) return rc;
     }
     ALB_CUDA_TRY(cudaGraphLaunch(w->exec, s));

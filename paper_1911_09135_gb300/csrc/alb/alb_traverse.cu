@@ -328,7 +328,8 @@ alb_status run_traversal(alb_graph g, App app, uint32_t src, uint32_t k, uint32_
   }
   if (g->params.exec_mode == 0) {
     if (!g->exec[app]) {
-      alb_status rc = build_graph(g, app);
+      alb_status rc = setup_barrier();
+      if (rc == ALB_OK) rc = build_graph(g, app);
       if (rc != ALB_OK) return rc;
     }
     ALB_CUDA_TRY(cudaGraphLaunch(g->exec[app], s));
@@ -408,16 +409,19 @@ namespace alb {
 
 constexpr uint32_t kNoAllocMaxVertices = 1u << 20;
 constexpr size_t kNoAllocVec = ((sizeof(uint32_t) * ((size_t)kNoAllocMaxVertices + 1) + 255) / 256) * 256;
-constexpr size_t kNoAllocBytes = 4 * kNoAllocVec + 3 * 256;
+constexpr size_t kNoAllocBytes = 4 * kNoAllocVec + 4 * 256;
 
 // Shared by every call on a device: calls whose work overlaps on the GPU race on it.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
+// Result of the CSR check: bit kBadOrder for offsets that decrease (a malformed argument),
+// bit kBadIndex for an index >= n (corrupt data); plus offsets[0] and offsets[n].
 struct NoAllocCheck {
   uint32_t bad;
   uint32_t off0;
   uint32_t offn;
 };
+constexpr uint32_t kBadOrder = 1u, kBadIndex = 2u;
 
 // One pass over the caller's CSR, so the traversal kernels never index out of range.
 __global__ void k_noalloc_check(const uint32_t* off, const uint32_t* idx, uint32_t n, uint64_t m,
@@ -426,10 +430,10 @@ __global__ void k_noalloc_check(const uint32_t* off, const uint32_t* idx, uint32
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   uint32_t bad = 0;
   for (uint64_t v = tid; v < n; v += stride)
-    if (off[v + 1] < off[v]) bad = 1;
+    if (off[v + 1] < off[v]) bad |= kBadOrder;
   for (uint64_t e = tid; e < m; e += stride)
-    if (idx[e] >= n) bad = 1;
-  if (bad) atomicOr(&out->bad, 1u);
+    if (idx[e] >= n) bad |= kBadIndex;
+  if (bad) atomicOr(&out->bad, bad);
   if (tid == 0) {
     out->off0 = off[0];
     out->offn = off[n];
@@ -479,6 +483,7 @@ extern "C" alb_status alb_bfs_noalloc(uint32_t n, uint64_t m, const uint32_t* d_
   RoundState* st = reinterpret_cast<RoundState*>(base + 4 * kNoAllocVec);
   CallArgs* args = reinterpret_cast<CallArgs*>(base + 4 * kNoAllocVec + 256);
   NoAllocCheck* chk = reinterpret_cast<NoAllocCheck*>(base + 4 * kNoAllocVec + 512);
+  uint32_t* bounds = reinterpret_cast<uint32_t*>(base + 4 * kNoAllocVec + 768);  // TravCtx::chk
   static_assert(sizeof(RoundState) <= 256 && sizeof(CallArgs) <= 256, "scratch layout");
 
   int dev = 0, sms = 0;
@@ -495,8 +500,8 @@ extern "C" alb_status alb_bfs_noalloc(uint32_t n, uint64_t m, const uint32_t* d_
   ALB_CUDA_TRY(cudaGetLastError());
   ALB_CUDA_TRY(cudaMemcpyAsync(&h, chk, sizeof(h), cudaMemcpyDeviceToHost, s));
   ALB_CUDA_TRY(cudaStreamSynchronize(s));
-  if (h.off0 != 0u || (uint64_t)h.offn != m) return ALB_ERR_INVALID_ARG;
-  if (h.bad) return ALB_ERR_DEVICE;
+  if (h.off0 != 0u || (uint64_t)h.offn != m || (h.bad & kBadOrder)) return ALB_ERR_INVALID_ARG;
+  if (h.bad & kBadIndex) return ALB_ERR_DEVICE;
 
   TravCtx c{};
   c.off = d_offsets;
@@ -517,10 +522,13 @@ extern "C" alb_status alb_bfs_noalloc(uint32_t n, uint64_t m, const uint32_t* d_
   c.pw = 0u;
   c.st = st;
   c.args = args;
+  c.m = (uint32_t)m;   // bound of the edge indices in the bounds-checked build
+  c.chk = bounds;      // the bounds-checked build's record (never written by the regular build)
 
   CallArgs ca{d_levels, src, 0u, nullptr, nullptr, nullptr};
   k_set_args<<<1, 1, 0, s>>>(args, ca);
   ALB_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(RoundState), s));  // counters must start at zero
+  ALB_CUDA_TRY(cudaMemsetAsync(bounds, 0, 4 * sizeof(uint32_t), s));
   void* kargs[] = {&c};
   ALB_CUDA_TRY(cudaLaunchKernel((void*)k_init<APP_BFS>, dim3(blocks), dim3(kBlock), kargs, 0, s));
   RoundState hs{};
@@ -536,5 +544,9 @@ extern "C" alb_status alb_bfs_noalloc(uint32_t n, uint64_t m, const uint32_t* d_
     if (hs.status & ST_ERR_ROUNDS) return ALB_ERR_TIMEOUT;
     if (hs.fcount[hs.round & 1u] == 0u) break;
   }
+  uint32_t rec[4] = {0u, 0u, 0u, 0u};
+  ALB_CUDA_TRY(cudaMemcpyAsync(rec, bounds, sizeof(rec), cudaMemcpyDeviceToHost, s));
+  ALB_CUDA_TRY(cudaStreamSynchronize(s));
+  if (rec[0] != 0u) return ALB_ERR_DEVICE;  // the bounds-checked build skipped an access
   return ALB_OK;
 }

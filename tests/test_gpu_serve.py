@@ -48,6 +48,47 @@ def test_results_alone_equal_results_in_the_mix(graphs, small_sms):
         assert np.array_equal(srv.results[r.rid], ref), (r.rid, r.kind)
 
 
+def test_config5_large_graphs_alone_equal_mix_equal_oracle():
+    """The two largest serving graphs that fit the test budget (RMAT scales 20 and 21, seeds 504
+    and 505, as in the 8-graph serving mix), a short Poisson mix at 2,000 requests/s: every
+    served result equals the same request run alone, and a sample of each kind equals the
+    oracle."""
+    from concurrent.futures import ThreadPoolExecutor
+    import os
+    big = [gg.rmat(sc, 16 << sc, 500 + i, symmetrize=True, weighted=True)
+           for i, sc in ((4, 20), (5, 21))]
+    reqs = serve.poisson_requests(big, 240, rate=2000.0, seed=5)
+    srv = serve.Server(big, tune=False, keep_results=True)
+    try:
+        assert len(srv.graphs[-1].slots) == 2        # m >= 50M: the larger graph has two slots
+        srv.run(reqs, realtime=True, timeout=300)
+        assert all(r.done >= r.arrival for r in reqs)
+        assert srv.batches < len(reqs)
+        _, alone = serve.one_at_a_time(srv, reqs, keep_results=True)
+    finally:
+        srv.close()
+    for r in reqs:
+        assert np.array_equal(srv.results[r.rid], alone[r.rid]), (r.rid, r.kind)
+    sample = []
+    for kind in serve.KINDS:
+        for gi in range(len(big)):
+            sample += [r for r in reqs if r.kind == kind and r.graph == gi][:2]
+
+    def ref(r):
+        g = big[r.graph]
+        if r.kind == "bfs":
+            return oracle.bfs(g.n, g.offsets, g.indices, r.src)
+        if r.kind == "sssp":
+            return oracle.sssp(g.n, g.offsets, g.indices, g.weights, r.src)
+        return oracle.cc(g.n, g.offsets, g.indices)
+
+    with ThreadPoolExecutor(max_workers=len(os.sched_getaffinity(0))) as ex:
+        refs = list(ex.map(ref, sample))
+    assert len(sample) >= 10
+    for r, want in zip(sample, refs):
+        assert np.array_equal(srv.results[r.rid], want), (r.rid, r.kind, r.graph)
+
+
 def test_admission_waits_for_free_device_memory(graphs):
     reqs = serve.poisson_requests(graphs, 40, rate=1e6, seed=6)
     srv = serve.Server(graphs, tune=False, keep_results=True)
