@@ -148,6 +148,15 @@ alb_status alb_graph_clone(alb_graph src, alb_graph* out);
 /* Free a graph and its workspace (waits for the whole device first). */
 alb_status alb_graph_destroy(alb_graph g);
 
+/* Release what the handle's calls allocated on first use and kept for the next call: the
+ * multi-source batch workspace and its worker clones, PageRank's per-graph inspection and
+ * vectors, the staging buffer of host outputs and every cached CUDA graph. The CSR and the round
+ * workspace stay, so the handle remains usable; the next call of each kind allocates again. A
+ * server uses it to give device memory back to other graphs under memory pressure. The paper has
+ * no counterpart (it runs one query at a time). Waits for the whole device first; *freed_bytes
+ * (may be NULL) receives the growth of the device's free memory. */
+alb_status alb_graph_trim(alb_graph g, uint64_t* freed_bytes);
+
 /* alb_set_params applies p to every application of the handle; alb_get_params returns the
  * bfs parameters. Per-application parameters: see alb_set_app_params below. Setting
  * parameters drops cached work and waits for the whole device first. */

@@ -36,7 +36,7 @@ EXPORTS = [
     "alb_bfs_multi", "alb_sssp_multi", "alb_autotune", "alb_set_app_params", "alb_get_app_params",
     "alb_graph_clone", "alb_debug_check", "alb_checked_build", "alb_get_cta_loads",
     "alb_partition_split", "alb_partition_sms", "alb_partition_stream_create",
-    "alb_partition_stream_destroy", "alb_partition_destroy",
+    "alb_partition_stream_destroy", "alb_partition_destroy", "alb_graph_trim",
 ]
 
 ALB_APP = {"bfs": 0, "sssp": 1, "cc": 2, "pr": 3, "pagerank": 3, "kcore": 4}
@@ -107,6 +107,7 @@ def load(build_if_missing: bool = False):
         "alb_graph_create": ([_U32, ctypes.c_uint64, _P, _P, _P, _U32, _P, ctypes.POINTER(_P)], S),
         "alb_graph_destroy": ([_P], S),
         "alb_graph_clone": ([_P, ctypes.POINTER(_P)], S),
+        "alb_graph_trim": ([_P, ctypes.POINTER(ctypes.c_uint64)], S),
         "alb_debug_check": ([_P, _P], S),
         "alb_get_cta_loads": ([_P, _P, _P, _U32, ctypes.POINTER(_U32), ctypes.POINTER(_U32)], S),
         "alb_checked_build": ([], _U32),
@@ -222,6 +223,13 @@ def alb_graph_clone(g) -> int:
 
 def alb_graph_destroy(g) -> None:
     _check(load().alb_graph_destroy(g), "alb_graph_destroy")
+
+
+def alb_graph_trim(g) -> int:
+    """Release the handle's cached per-call workspaces; returns the bytes the device got back."""
+    freed = ctypes.c_uint64(0)
+    _check(load().alb_graph_trim(g, ctypes.byref(freed)), "alb_graph_trim")
+    return int(freed.value)
 
 
 def alb_default_params() -> alb_params:
@@ -425,6 +433,10 @@ class Graph:
         if getattr(self, "h", None):
             alb_graph_destroy(self.h)
             self.h = None
+
+    def trim(self) -> int:
+        """Release cached per-call workspaces (the CSR stays); bytes given back."""
+        return alb_graph_trim(self.h)
 
     def __del__(self):
         try:

@@ -376,6 +376,24 @@ alb_status alb_graph_destroy(alb_graph g) {
   return ALB_OK;
 }
 
+alb_status alb_graph_trim(alb_graph g, uint64_t* freed_bytes) {
+  if (!g) return ALB_ERR_INVALID_ARG;
+  if (cudaSetDevice(g->device) != cudaSuccess) return ALB_ERR_CUDA;
+  size_t before = 0, after = 0, total = 0;
+  // the handle's calls may still run on several streams: nothing may use what is freed
+  ALB_CUDA_TRY(cudaDeviceSynchronize());
+  ALB_CUDA_TRY(cudaMemGetInfo(&before, &total));
+  free_traversal_graphs(g);
+  free_pagerank(g);
+  free_batch(g);
+  cudaFree(g->tmp);
+  g->tmp = nullptr;
+  cudaGetLastError();
+  ALB_CUDA_TRY(cudaMemGetInfo(&after, &total));
+  if (freed_bytes) *freed_bytes = after > before ? (uint64_t)(after - before) : 0u;
+  return ALB_OK;
+}
+
 alb_status alb_set_params(alb_graph g, const alb_params* p) {
   if (!g || !p || !params_valid(p)) return ALB_ERR_INVALID_ARG;
   cudaSetDevice(g->device);
