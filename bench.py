@@ -904,7 +904,9 @@ def serve_arm(args, dist):
             "steps": 1, "warmup": 1, "ms_per_step": round(wall * 1e3, 1),
             "step": "the whole open-loop run of the Poisson requests", "clocks": region.clocks,
             "latency": lat, "gteps": round(gteps, 3), "offered_rate": 2000.0, "requests": len(reqs),
-            "wall_s": round(wall, 3), "deferred_admissions": srv.deferred, "per_graph": per_graph,
+            "wall_s": round(wall, 3), "deferred_admissions": srv.deferred,
+            "evictions": srv.evictions, "slots_admitted_while_serving": srv.admitted_slots,
+            "per_graph": per_graph,
             "below_saturation": below,
             "saturation": {"requests": len(sat), "batched_s": round(t_batched, 3), "batches": nb,
                            "one_at_a_time_s": round(t_plain, 3),

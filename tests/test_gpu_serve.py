@@ -89,21 +89,40 @@ def test_config5_large_graphs_alone_equal_mix_equal_oracle():
         assert np.array_equal(srv.results[r.rid], want), (r.rid, r.kind, r.graph)
 
 
-def test_admission_waits_for_free_device_memory(graphs):
-    reqs = serve.poisson_requests(graphs, 40, rate=1e6, seed=6)
-    srv = serve.Server(graphs, tune=False, keep_results=True)
+def test_lazy_slots_wait_for_free_device_memory_then_serve_in_order(graphs):
+    """Slots set up on first use (lazy): the free memory the server sees is held below what the
+    first batches need for a while (an injected cudaMemGetInfo: another user of the device), so
+    they are deferred and stay queued; once memory frees up they are admitted in arrival order,
+    their buffers and workspaces are set up, and every result equals the oracle."""
+    real = torch.cuda.mem_get_info
+    calls = {"n": 0}
+
+    def squeezed():
+        calls["n"] += 1
+        free, total = real()
+        return (0 if calls["n"] <= 50 else free), total
+
+    reqs = serve.poisson_requests(graphs, 60, rate=1e6, seed=6)
+    srv = serve.Server(graphs, tune=False, keep_results=True, lazy=True, mem_get_info=squeezed,
+                       hbm_reserve=1 << 28)
     try:
-        srv.reserve = 1 << 60                           # nothing fits
-        gr = srv.graphs[reqs[0].graph]
-        gr.queue[reqs[0].kind].append(reqs[0])
-        assert srv._launch(gr, gr.slots[0]) is False and srv.deferred == 1
-        assert len(gr.queue[reqs[0].kind]) == 1         # the request is still queued
-        gr.queue[reqs[0].kind].clear()
-        srv.reserve = 0
-        srv.run(reqs, realtime=False, timeout=60)
-        assert all(r.done >= 0 for r in reqs)
+        srv.run(reqs, realtime=False, timeout=120)
     finally:
         srv.close()
+    assert srv.deferred >= 1 and all(r.done >= 0 for r in reqs)
+    by = {}
+    for gid, kind, rid in srv.admit_log:
+        by.setdefault((gid, kind), []).append(rid)
+    assert all(v == sorted(v) for v in by.values())
+    for r in reqs:
+        g = graphs[r.graph]
+        if r.kind == "bfs":
+            ref = oracle.bfs(g.n, g.offsets, g.indices, r.src)
+        elif r.kind == "sssp":
+            ref = oracle.sssp(g.n, g.offsets, g.indices, g.weights, r.src)
+        else:
+            ref = oracle.cc(g.n, g.offsets, g.indices)
+        assert np.array_equal(srv.results[r.rid], ref), (r.rid, r.kind)
 
 
 def test_sm_partition_streams_run_the_library_exactly(graphs):
