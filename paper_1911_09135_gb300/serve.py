@@ -381,7 +381,10 @@ class Server:
         be = self.backend
         self.tune = tune
         self.ctas_per_sm = ctas_per_sm
-        self.adm = Admission(mem_get_info or be.mem_get_info, hbm_reserve, be.cached)
+        # an injected mem_get_info replaces the whole view of free memory (the device's free
+        # bytes and the caching allocator's idle blocks)
+        self.adm = (Admission(mem_get_info, hbm_reserve) if mem_get_info is not None
+                    else Admission(be.mem_get_info, hbm_reserve, be.cached))
         # smaller graphs get higher stream priority, so their short rounds are scheduled
         # between the round kernels of large graphs instead of waiting behind them
         lo, hi = be.priority_range()
