@@ -127,6 +127,9 @@ def parse_args():
     ap.add_argument("--small-sms", type=int, default=0,
                     help="serve: an SM partition of this many SMs for the small graphs (0 = none)")
     ap.add_argument("--big-slots", type=int, default=2, help="serve: slots per large graph")
+    ap.add_argument("--batch-scale", type=int, default=22,
+                    help="batch-sources: RMAT scale of the graph (22 = the batched configuration; "
+                         "smaller scales for profiling captures)")
     return ap.parse_args()
 
 
@@ -726,10 +729,12 @@ def batch_arm(args, dist):
         return e0.elapsed_time(e1) / reps
 
     res = {}
+    host_loop = args.exec_mode == "host"
     region = TimedRegion(dist)
     region.__enter__()
     if args.workload == "batch-sources":
-        g = gg.rmat22_sym()
+        g = (gg.rmat22_sym() if args.batch_scale == 22 else
+             gg.rmat(args.batch_scale, 16 << args.batch_scale, 2, symmetrize=True, weighted=True))
         rng = np.random.Generator(np.random.Philox(key=4))
         srcs = rng.integers(0, g.n, size=128).astype(np.uint32)
         d_srcs = dev(srcs)
@@ -741,7 +746,11 @@ def batch_arm(args, dist):
         n = g.n
         for app, single, batch in (("bfs", alb.alb_bfs, alb.alb_bfs_batch),
                                    ("sssp", alb.alb_sssp, alb.alb_sssp_batch)):
+            if args.apps and app not in args.apps.split(","):
+                continue
             tuned, _ = G.autotune(app, tune_source(g, int(srcs[0])), reps=2)  # the plain path's knobs
+            if host_loop:  # one launch per kernel (profiling captures)
+                G.set_app_params(app, exec_mode=1)
             def plain():
                 for i, s in enumerate(srcs.tolist()):
                     single(G.h, s, out[i * n:(i + 1) * n])
@@ -764,7 +773,8 @@ def batch_arm(args, dist):
                         "batched_hub_threshold": t_best,
                         "queries_per_s_batched": round(128 / (ms_batch * 1e-3), 1)}
         G.close()
-        desc = "128 sources (seed 4) on rmat22-sym (scale 22, ef 16, seed 2, w in [1,100])"
+        desc = (f"128 sources (seed 4) on rmat{args.batch_scale}-sym (scale {args.batch_scale}, ef 16, "
+                f"seed 2, w in [1,100])" + (", host-loop execution" if host_loop else ""))
     else:
         parts = gg.small_graphs(512, seed=4)
         u, base = gg.disjoint_union(parts)

@@ -94,7 +94,9 @@ typedef struct {
   uint32_t grid_blocks;    /* CTAs of every round kernel; 0 = SMs x resident CTAs per SM of each kernel
                             * (PageRank's pull kernel: 8 such waves) */
   uint32_t distribution;   /* LB edge distribution: 0 cyclic (default), 1 blocked (Sec. 4.1) */
-  uint32_t exec_mode;      /* 0: device-side round loop in a CUDA graph (default); 1: host loop */
+  uint32_t exec_mode;      /* 0: device-side round loop in a CUDA graph (default); 1: host loop
+                            * (one launch per kernel, the round state read by the host after each;
+                            * batched calls then run their groups one after another) */
   uint32_t max_rounds;     /* 0: n + 1 (enough for every app); ALB_ERR_TIMEOUT when reached */
   float l2_persist_fraction; /* > 0 (CUDA-graph mode): the labels get an L2 access-policy window
                               * whose hits persist in this share of the device's persisting L2

@@ -329,6 +329,54 @@ static alb_status add_node(cudaGraphNode_t* node, cudaGraph_t graph, const cudaG
   return ALB_OK;
 }
 
+// Kernels and grids of one batch kind on handle g: init, seed, the round kernels and their
+// persistent grids (sized from the round kernels' own residency: the multi-source operators hold
+// more registers than the single-source ones the handle's grids are sized for); the paper's
+// threshold rule follows this LB grid.
+struct BatchCfg {
+  void *init, *seed, *insp, *lb;
+  uint32_t seed_grid, seed_block, ib, lbb, threshold;
+};
+
+static BatchCfg batch_cfg(alb_graph g, BatchKind kind) {
+  BatchCfg k{};
+  k.seed_grid = 1;
+  k.seed_block = 32;
+  switch (kind) {
+    case BK_MS_BFS:
+      k.init = (void*)k_batch_init; k.seed = (void*)k_batch_seed;
+      k.insp = (void*)k_inspect<MsBfsOp>; k.lb = (void*)k_lb<MsBfsOp, false>;
+      break;
+    case BK_MS_SSSP:
+      k.init = (void*)k_batch_init; k.seed = (void*)k_batch_seed;
+      k.insp = (void*)k_inspect<MsSsspOp>; k.lb = (void*)k_lb<MsSsspOp, false>;
+      break;
+    case BK_MULTI_BFS:
+      k.init = (void*)k_multi_init<APP_BFS>; k.seed = (void*)k_multi_seed;
+      k.insp = (void*)k_inspect<BfsOp>; k.lb = (void*)k_lb<BfsOp, false>;
+      k.seed_grid = g->blocks; k.seed_block = kBlock;
+      break;
+    default:
+      k.init = (void*)k_multi_init<APP_SSSP>; k.seed = (void*)k_multi_seed;
+      k.insp = (void*)k_inspect<SsspOp>; k.lb = (void*)k_lb<SsspOp, false>;
+      k.seed_grid = g->blocks; k.seed_block = kBlock;
+      break;
+  }
+  k.ib = g->blocks;
+  k.lbb = g->lb_blocks;
+  k.threshold = g->threshold;
+  if (!g->params.grid_blocks) {
+    int bi = 0, bl = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bi, k.insp, kBlock, 0) == cudaSuccess && bi > 0)
+      k.ib = (uint32_t)g->num_sms * (uint32_t)bi;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, k.lb, kBlock, 0) == cudaSuccess && bl > 0)
+      k.lbb = (uint32_t)g->num_sms * (uint32_t)bl;
+    cudaGetLastError();
+    if (g->params.hub_threshold < 0) k.threshold = k.lbb * (uint32_t)kBlock;
+  }
+  return k;
+}
+
 // memset(state) -> init -> seed -> while { inspect -> if (work) lb } [-> transpose]
 static alb_status build_batch_graph(alb_graph g, BatchKind kind) {
   BatchWs* b = g->batch;
@@ -340,41 +388,10 @@ static alb_status build_batch_graph(alb_graph g, BatchKind kind) {
       cudaGraphConditionalHandleCreate(&hi, G, 0u, cudaGraphCondAssignDefault) != cudaSuccess)
     return fail(ALB_ERR_CUDA);
   TravCtx c = make_ctx(g, true, hw, hi);
-  void *init, *seed, *insp, *lb;
-  uint32_t seed_grid = 1, seed_block = 32;
-  switch (kind) {
-    case BK_MS_BFS:
-      init = (void*)k_batch_init; seed = (void*)k_batch_seed;
-      insp = (void*)k_inspect<MsBfsOp>; lb = (void*)k_lb<MsBfsOp, false>;
-      break;
-    case BK_MS_SSSP:
-      init = (void*)k_batch_init; seed = (void*)k_batch_seed;
-      insp = (void*)k_inspect<MsSsspOp>; lb = (void*)k_lb<MsSsspOp, false>;
-      break;
-    case BK_MULTI_BFS:
-      init = (void*)k_multi_init<APP_BFS>; seed = (void*)k_multi_seed;
-      insp = (void*)k_inspect<BfsOp>; lb = (void*)k_lb<BfsOp, false>;
-      seed_grid = g->blocks; seed_block = kBlock;
-      break;
-    default:
-      init = (void*)k_multi_init<APP_SSSP>; seed = (void*)k_multi_seed;
-      insp = (void*)k_inspect<SsspOp>; lb = (void*)k_lb<SsspOp, false>;
-      seed_grid = g->blocks; seed_block = kBlock;
-      break;
-  }
-  // the round kernels' persistent grids from their own residency (the multi-source operators
-  // hold more registers than the single-source ones the handle's grids are sized for); the
-  // paper's threshold rule follows this LB grid
-  uint32_t ib = g->blocks, lbb = g->lb_blocks;
-  if (!g->params.grid_blocks) {
-    int bi = 0, bl = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bi, insp, kBlock, 0) == cudaSuccess && bi > 0)
-      ib = (uint32_t)g->num_sms * (uint32_t)bi;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, lb, kBlock, 0) == cudaSuccess && bl > 0)
-      lbb = (uint32_t)g->num_sms * (uint32_t)bl;
-    cudaGetLastError();
-    if (g->params.hub_threshold < 0) c.threshold = lbb * (uint32_t)kBlock;
-  }
+  const BatchCfg k = batch_cfg(g, kind);
+  void *init = k.init, *seed = k.seed, *insp = k.insp, *lb = k.lb;
+  const uint32_t seed_grid = k.seed_grid, seed_block = k.seed_block, ib = k.ib, lbb = k.lbb;
+  c.threshold = k.threshold;
   cudaGraphNode_t n_ms, n_init, n_seed, n_while, n_insp, n_if, n_lb, n_out;
   cudaMemsetParams ms{};
   ms.dst = g->st;
@@ -429,6 +446,54 @@ static alb_status stage_srcs(alb_graph g, const uint32_t* hd_srcs, uint32_t k, c
   return ALB_OK;
 }
 
+// The same launch sequence as the batch graph, driven by the host (exec_mode 1): one launch per
+// kernel, the round state read after each round kernel; with profile = 1 every round kernel is
+// timed with CUDA events. ncu profiles these launches, not kernels inside graphs with
+// conditional nodes.
+static alb_status batch_host_loop(alb_graph g, BatchKind kind, cudaStream_t s) {
+  const BatchCfg k = batch_cfg(g, kind);
+  TravCtx c = make_ctx(g, false, 0, 0);
+  c.threshold = k.threshold;
+  const bool prof = g->params.profile != 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (prof) { cudaEventCreate(&e0); cudaEventCreate(&e1); }
+  auto launch = [&](void* fn, uint32_t grid, uint32_t block, double* ms, uint32_t* cnt) -> alb_status {
+    void* args[] = {&c};
+    if (prof && ms) cudaEventRecord(e0, s);
+    ALB_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, 0, s));
+    if (prof && ms) {
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      *ms += t;
+      *cnt += 1;
+    }
+    return ALB_OK;
+  };
+  alb_status rc = ALB_OK;
+  ALB_CUDA_TRY(cudaMemsetAsync(g->st, 0, sizeof(RoundState), s));
+  if ((rc = launch(k.init, g->blocks, kBlock, nullptr, nullptr)) != ALB_OK) return rc;
+  if ((rc = launch(k.seed, k.seed_grid, k.seed_block, nullptr, nullptr)) != ALB_OK) return rc;
+  for (;;) {
+    if ((rc = launch(k.insp, k.ib, kBlock, &g->stats.ms_inspect, &g->stats.n_inspect)) != ALB_OK) return rc;
+    ALB_CUDA_TRY(cudaMemcpyAsync(g->h_st, g->st, sizeof(RoundState), cudaMemcpyDeviceToHost, s));
+    ALB_CUDA_TRY(cudaStreamSynchronize(s));
+    if (g->h_st->hub_packed >> 32) {
+      if ((rc = launch(k.lb, k.lbb, kBlock, &g->stats.ms_lb, &g->stats.n_lb)) != ALB_OK) return rc;
+      ALB_CUDA_TRY(cudaMemcpyAsync(g->h_st, g->st, sizeof(RoundState), cudaMemcpyDeviceToHost, s));
+      ALB_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    const RoundState& h = *g->h_st;
+    if (h.status || h.fcount[h.round & 1u] == 0u) break;
+  }
+  if (kind == BK_MS_BFS || kind == BK_MS_SSSP)
+    if ((rc = launch((void*)k_batch_out, g->blocks, kBlock, nullptr, nullptr)) != ALB_OK) return rc;
+  if (prof) { cudaEventDestroy(e0); cudaEventDestroy(e1); }
+  ALB_CUDA_TRY(cudaGetLastError());
+  return ALB_OK;
+}
+
 // One group of ns <= 32 sources (device list) on handle h and stream s, into dst (device).
 static alb_status run_group_on(alb_graph h, BatchKind kind, const uint32_t* d_srcs, uint32_t ns, uint32_t* dst,
                                cudaStream_t s) {
@@ -479,13 +544,15 @@ static alb_status run_groups(alb_graph g, BatchKind kind, const uint32_t* hd_src
   if (rc != ALB_OK) return rc;
   BatchWs* b = g->batch;
   if ((rc = stage_srcs(g, hd_srcs, k, s)) != ALB_OK) return rc;
-  if (!b->exec[kind] && ((rc = setup_barrier()) != ALB_OK || (rc = build_batch_graph(g, kind)) != ALB_OK))
+  const bool host_loop = g->params.exec_mode == 1;
+  if (!host_loop && !b->exec[kind] &&
+      ((rc = setup_barrier()) != ALB_OK || (rc = build_batch_graph(g, kind)) != ALB_OK))
     return rc;
   const bool dev = is_device_ptr(out);
   const size_t n = g->n;
   const uint32_t ngroups = (k + 31u) / 32u;
   b->used_workers = 0;
-  if (dev && ngroups > 1) {
+  if (dev && ngroups > 1 && !host_loop) {
     // several groups with a device output: deal them over the handle and its worker clones
     const uint32_t W = ngroups < kBatchWorkers ? ngroups : kBatchWorkers;
     const int app = kind == BK_MS_BFS ? ALB_APP_BFS : ALB_APP_SSSP;
@@ -520,7 +587,11 @@ static alb_status run_groups(alb_graph g, BatchKind kind, const uint32_t* hd_src
     CallArgs ca{dst, 0u, 0u, nullptr, nullptr, nullptr, b->aux, b->srcs + g0, ns};
     k_set_args<<<1, 1, 0, s>>>(g->args, ca);
     ALB_CUDA_TRY(cudaGetLastError());
-    ALB_CUDA_TRY(cudaGraphLaunch(b->exec[kind], s));
+    if (host_loop) {
+      if ((rc = batch_host_loop(g, kind, s)) != ALB_OK) return rc;
+    } else {
+      ALB_CUDA_TRY(cudaGraphLaunch(b->exec[kind], s));
+    }
     if (!dev)
       ALB_CUDA_TRY(cudaMemcpyAsync(out + (size_t)g0 * n, b->tmp, sizeof(uint32_t) * n * ns,
                                    cudaMemcpyDeviceToHost, s));
@@ -536,7 +607,9 @@ static alb_status run_multi(alb_graph g, BatchKind kind, const uint32_t* hd_srcs
   if (rc != ALB_OK) return rc;
   BatchWs* b = g->batch;
   if ((rc = stage_srcs(g, hd_srcs, k, s)) != ALB_OK) return rc;
-  if (!b->exec[kind] && ((rc = setup_barrier()) != ALB_OK || (rc = build_batch_graph(g, kind)) != ALB_OK))
+  const bool host_loop = g->params.exec_mode == 1;
+  if (!host_loop && !b->exec[kind] &&
+      ((rc = setup_barrier()) != ALB_OK || (rc = build_batch_graph(g, kind)) != ALB_OK))
     return rc;
   const bool dev = is_device_ptr(out);
   uint32_t* lab = out;
@@ -547,7 +620,11 @@ static alb_status run_multi(alb_graph g, BatchKind kind, const uint32_t* hd_srcs
   CallArgs ca{lab, 0u, 0u, nullptr, nullptr, nullptr, nullptr, b->srcs, k};
   k_set_args<<<1, 1, 0, s>>>(g->args, ca);
   ALB_CUDA_TRY(cudaGetLastError());
-  ALB_CUDA_TRY(cudaGraphLaunch(b->exec[kind], s));
+  if (host_loop) {
+    if ((rc = batch_host_loop(g, kind, s)) != ALB_OK) return rc;
+  } else {
+    ALB_CUDA_TRY(cudaGraphLaunch(b->exec[kind], s));
+  }
   if (!dev) ALB_CUDA_TRY(cudaMemcpyAsync(out, lab, sizeof(uint32_t) * g->n, cudaMemcpyDeviceToHost, s));
   g->last_stream = s;
   g->last_kind = 0;
@@ -557,6 +634,13 @@ static alb_status run_multi(alb_graph g, BatchKind kind, const uint32_t* hd_srcs
 }  // namespace alb
 
 using namespace alb;
+
+// A batched call starts the per-kernel timers of alb_stats afresh (profile = 1, host loop).
+static void begin_batch(alb_graph g, int app) {
+  select_cfg(g, app);
+  g->stats.ms_inspect = g->stats.ms_lb = g->stats.ms_other = 0.0;
+  g->stats.n_inspect = g->stats.n_lb = g->stats.n_other = 0;
+}
 
 static alb_status sssp_ok(alb_graph g) {
   if (!g->has_w) return ALB_ERR_UNSUPPORTED;
@@ -569,7 +653,7 @@ extern "C" alb_status alb_bfs_batch(alb_graph g, const uint32_t* hd_srcs, uint32
   if (!g || (k && (!hd_srcs || !hd_out))) return ALB_ERR_INVALID_ARG;
   if (k == 0) return ALB_OK;
   if (cudaSetDevice(g->device) != cudaSuccess) return ALB_ERR_CUDA;
-  select_cfg(g, ALB_APP_BFS);
+  begin_batch(g, ALB_APP_BFS);
   return run_groups(g, BK_MS_BFS, hd_srcs, k, hd_out, (cudaStream_t)stream);
 }
 
@@ -580,7 +664,7 @@ extern "C" alb_status alb_sssp_batch(alb_graph g, const uint32_t* hd_srcs, uint3
   if (rc != ALB_OK) return rc;
   if (k == 0) return ALB_OK;
   if (cudaSetDevice(g->device) != cudaSuccess) return ALB_ERR_CUDA;
-  select_cfg(g, ALB_APP_SSSP);
+  begin_batch(g, ALB_APP_SSSP);
   return run_groups(g, BK_MS_SSSP, hd_srcs, k, hd_out, (cudaStream_t)stream);
 }
 
@@ -588,7 +672,7 @@ extern "C" alb_status alb_bfs_multi(alb_graph g, const uint32_t* hd_srcs, uint32
                                     alb_stream stream) {
   if (!g || !hd_srcs || !hd_levels || k == 0) return ALB_ERR_INVALID_ARG;
   if (cudaSetDevice(g->device) != cudaSuccess) return ALB_ERR_CUDA;
-  select_cfg(g, ALB_APP_BFS);
+  begin_batch(g, ALB_APP_BFS);
   return run_multi(g, BK_MULTI_BFS, hd_srcs, k, hd_levels, (cudaStream_t)stream);
 }
 
@@ -598,6 +682,6 @@ extern "C" alb_status alb_sssp_multi(alb_graph g, const uint32_t* hd_srcs, uint3
   alb_status rc = sssp_ok(g);
   if (rc != ALB_OK) return rc;
   if (cudaSetDevice(g->device) != cudaSuccess) return ALB_ERR_CUDA;
-  select_cfg(g, ALB_APP_SSSP);
+  begin_batch(g, ALB_APP_SSSP);
   return run_multi(g, BK_MULTI_SSSP, hd_srcs, k, hd_dist, (cudaStream_t)stream);
 }

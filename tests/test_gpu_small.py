@@ -298,12 +298,14 @@ def test_batch_matches_single_source(rmat13):
     G.close()
 
 
+@pytest.mark.parametrize("exec_mode", [0, 1])
 @pytest.mark.parametrize("t", [-1, 0, 64, 1 << 33])
-def test_batch_groups_ragged_and_duplicates(rmat13, t):
-    """40 sources = a full group of 32 and a ragged group of 8, with repeated sources."""
+def test_batch_groups_ragged_and_duplicates(rmat13, t, exec_mode):
+    """40 sources = a full group of 32 and a ragged group of 8, with repeated sources; in the
+    CUDA-graph mode and the host loop (one launch per kernel)."""
     g = rmat13
     G = make(g)
-    G.set_params(hub_threshold=t)
+    G.set_params(hub_threshold=t, exec_mode=exec_mode, profile=exec_mode)
     rng = np.random.default_rng(7)
     srcs = rng.integers(0, g.n, size=40).astype(np.uint32)
     srcs[5] = srcs[3]
@@ -313,6 +315,9 @@ def test_batch_groups_ragged_and_duplicates(rmat13, t):
     res = host(out).reshape(len(srcs), g.n).copy()
     G.sssp_batch(srcs, out)
     res2 = host(out).reshape(len(srcs), g.n).copy()
+    if exec_mode == 1:
+        st = G.stats()   # the host loop times every round kernel of the last group
+        assert st["n_inspect"] == st["rounds"] and st["ms_inspect"] > 0
     for i, s in enumerate(srcs):
         assert np.array_equal(res[i], oracle.bfs(g.n, g.offsets, g.indices, int(s))), i
         assert np.array_equal(res2[i], oracle.sssp(g.n, g.offsets, g.indices, g.weights, int(s))), i
@@ -341,15 +346,15 @@ def test_multi_source_is_min_over_sources(rmat13):
     G.close()
 
 
-@pytest.mark.parametrize("t", [-1, 0, 1 << 33])
-def test_disjoint_union_of_many_graphs(t):
+@pytest.mark.parametrize("t,exec_mode", [(-1, 0), (0, 0), (1 << 33, 0), (-1, 1)])
+def test_disjoint_union_of_many_graphs(t, exec_mode):
     rng = np.random.default_rng(3)
     parts = [gg.rmat(int(sc), int(16 << sc), 100 + i, symmetrize=True, weighted=True)
              for i, sc in enumerate(rng.integers(4, 11, size=25))]
     parts += [graphs.star(40), graphs.path(30), graphs.empty(3)]
     u, base = gg.disjoint_union(parts)
     G = make(u)
-    G.set_params(hub_threshold=t)
+    G.set_params(hub_threshold=t, exec_mode=exec_mode)
     srcs = base[:-1].astype(np.uint32)  # vertex 0 of every graph
     lv = G.bfs_multi(srcs)
     d = G.sssp_multi(srcs)
