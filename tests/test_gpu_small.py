@@ -316,8 +316,8 @@ def test_batch_groups_ragged_and_duplicates(rmat13, t, exec_mode):
     G.sssp_batch(srcs, out)
     res2 = host(out).reshape(len(srcs), g.n).copy()
     if exec_mode == 1:
-        st = G.stats()   # the host loop times every round kernel of the last group
-        assert st["n_inspect"] == st["rounds"] and st["ms_inspect"] > 0
+        st = G.stats()   # the host loop times every round kernel of both groups
+        assert st["n_inspect"] > st["rounds"] > 0 and st["ms_inspect"] > 0   # rounds: the last group's
     for i, s in enumerate(srcs):
         assert np.array_equal(res[i], oracle.bfs(g.n, g.offsets, g.indices, int(s))), i
         assert np.array_equal(res2[i], oracle.sssp(g.n, g.offsets, g.indices, g.weights, int(s))), i
