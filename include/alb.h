@@ -209,7 +209,7 @@ alb_status alb_kcore(alb_graph g, uint32_t k, uint32_t* hd_in_core, alb_stream s
  * device, an invalid one is skipped and ALB_ERR_INVALID_ARG is returned by alb_sync. Sources
  * in pinned host memory are copied asynchronously: keep them unchanged until the stream has
  * passed the call. Workspace:
- * 32 labels + a mask and two tagged masks per vertex (148 bytes x n), allocated on first use.
+ * 32 labels, a seen mask and three round masks per vertex (144 bytes x n), allocated on first use.
  * With more than 32 sources and a device output, the groups run concurrently: the handle takes
  * one and up to three worker clones of it (sharing its CSR; each with its own round and batch
  * workspace, CUDA graphs and stream, about 170 bytes x n) the others. The workers are made and

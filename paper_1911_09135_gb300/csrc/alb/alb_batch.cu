@@ -9,8 +9,8 @@
 //     operator differs:
 //       bfs : bit-parallel (a `seen` mask per vertex; one atomicOr discovers up to 32 sources),
 //       sssp: per active source, the relaxation of Fig. 3 with atomicMin.
-//     The per-round masks live in two round-tagged 64-bit arrays ((round << 32) | mask), so a
-//     stale entry never needs clearing.
+//     The per-round masks live in three 32-bit arrays used in rotation (read, written, cleared
+//     for the round after next), so a mask is merged with one atomicOr.
 // (2) Many small graphs (alb_bfs_multi, alb_sssp_multi): a traversal from a set of sources at
 //     distance 0. Run on the disjoint union of many graphs with one source in each, it computes
 //     every graph's own result in one launch sequence (components never interact).
@@ -22,44 +22,46 @@
 namespace alb {
 
 struct BatchAux {
-  uint32_t* lab;              // n x 32, vertex-major
-  uint32_t* seen;             // n: sources that reached v (bfs)
-  unsigned long long* act0;   // round-tagged masks, read in even rounds
-  unsigned long long* act1;   // ... odd rounds
+  uint32_t* lab;     // n x 32, vertex-major
+  uint32_t* seen;    // n: sources that reached v (bfs)
+  uint32_t* act[3];  // per-vertex source masks; round r reads act[r % 3], writes act[(r + 1) % 3]
+                     // and clears act[(r + 2) % 3], which round r - 1 read and round r + 1 writes
 };
 
-__device__ __forceinline__ unsigned long long* act_of(const BatchAux* x, uint32_t round) {
-  return (round & 1u) ? x->act1 : x->act0;
-}
+__device__ __forceinline__ uint32_t* act_of(const BatchAux* x, uint32_t round) { return x->act[round % 3u]; }
 
-// Sources for which v is active in round r (written during round r - 1 with tag r).
+// Sources for which v is active in round r (written during round r - 1).
 __device__ __forceinline__ uint32_t act_mask(const BatchAux* x, uint32_t r, uint32_t v) {
-  const unsigned long long t = act_of(x, r)[v];
-  return ((uint32_t)(t >> 32) == r) ? (uint32_t)t : 0u;
+  return act_of(x, r)[v];
 }
 
-// OR `bits` into the entry for round `tag`; true if the entry had no bit of that round before
-// (the caller then appends the vertex to the next frontier exactly once).
-__device__ __forceinline__ bool act_or(unsigned long long* p, uint32_t tag, uint32_t bits) {
-  // A cached read may be stale, but an entry only gains bits within a round: if it already
-  // holds all of `bits` for this round they are really there; otherwise the CAS below
-  // corrects a stale guess.
-  unsigned long long old = *p, assumed;
-  do {
-    assumed = old;
-    const uint32_t ot = (uint32_t)(assumed >> 32), om = (uint32_t)assumed;
-    const uint32_t nm = (ot == tag) ? (om | bits) : bits;
-    if (ot == tag && nm == om) return false;
-    old = atomicCAS(p, assumed, ((unsigned long long)tag << 32) | nm);
-  } while (old != assumed);
-  // zero-initialised entries carry tag 0 with an empty mask
-  return (uint32_t)(assumed >> 32) != tag || (uint32_t)assumed == 0u;
+// OR `bits` into v's mask for the next round; true for exactly one caller per vertex and round:
+// the one that set its first bit (it appends the vertex to the next frontier). A plain read
+// skips the atomic when every bit is already there (an entry only gains bits within a round,
+// so a stale read can only under-report them). A single atomicOr per update: many relaxations
+// of the same round often reach the same high-degree vertex, and a compare-and-swap loop there
+// serialises into a retry storm that keeps one warp spinning while the SMs idle.
+__device__ __forceinline__ bool act_or(uint32_t* p, uint32_t bits) {
+  const uint32_t cur = *p;
+  if ((cur & bits) == bits) return false;
+  return atomicOr(p, bits) == 0u;
+}
+
+// Round r's clearing of the mask array round r + 1 writes (see BatchAux): a grid-stride loop of
+// every CTA of the round's inspection kernel.
+__device__ __forceinline__ void act_clear(const BatchAux* x, uint32_t r, uint32_t n) {
+  uint32_t* c = act_of(x, r + 2u);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    c[i] = 0u;
 }
 
 // Multi-source bfs: sval is the vertex's source mask.
 struct MsBfsOp {
   static constexpr bool kBatch = true;
   static constexpr bool kW = false;
+  __device__ static void round_start(const OpArgs& a, uint32_t r) {
+    act_clear(static_cast<const BatchAux*>(a.aux), r, a.n);
+  }
   __device__ static uint32_t sval(const OpArgs& a, uint32_t v) {
     return act_mask(static_cast<const BatchAux*>(a.aux), a.next - 1u, v);
   }
@@ -72,7 +74,7 @@ struct MsBfsOp {
     if (!nw) return false;
     uint32_t* row = x->lab + (size_t)dst * 32u;
     for (uint32_t b = nw; b; b &= b - 1u) row[__ffs(b) - 1] = a.next;
-    return act_or(act_of(x, a.next) + dst, a.next, nw);
+    return act_or(act_of(x, a.next) + dst, nw);
   }
 };
 
@@ -84,6 +86,9 @@ struct MsBfsOp {
 struct MsSsspOp {
   static constexpr bool kBatch = true;
   static constexpr bool kW = true;
+  __device__ static void round_start(const OpArgs& a, uint32_t r) {
+    act_clear(static_cast<const BatchAux*>(a.aux), r, a.n);
+  }
   __device__ static uint32_t sval(const OpArgs&, uint32_t v) { return v; }
   __device__ static bool apply(const OpArgs& a, uint32_t v, uint32_t dst, uint32_t w) {
     const BatchAux* x = static_cast<const BatchAux*>(a.aux);
@@ -108,7 +113,7 @@ struct MsSsspOp {
         nb |= 1u << s1;
       }
     }
-    return nb && act_or(act_of(x, a.next) + dst, a.next, nb);
+    return nb && act_or(act_of(x, a.next) + dst, nb);
   }
 };
 
@@ -119,8 +124,9 @@ __device__ __forceinline__ bool aux_ok(const TravCtx& c, const BatchAux* x) {
 #ifdef ALB_CHECKED
   const uint64_t a = (uint64_t)x;
   if (!ALB_IN_RANGE(c.chk, CHK_PTR, (a == 0 || (a & 7)) ? 1u : 0u, 1u)) return false;
-  const uint64_t l = (uint64_t)x->lab, s = (uint64_t)x->seen, p0 = (uint64_t)x->act0, p1 = (uint64_t)x->act1;
-  const bool bad = !l || (l & 3) || !s || (s & 3) || !p0 || (p0 & 7) || !p1 || (p1 & 7);
+  const uint64_t l = (uint64_t)x->lab, s = (uint64_t)x->seen;
+  const uint64_t p0 = (uint64_t)x->act[0], p1 = (uint64_t)x->act[1], p2 = (uint64_t)x->act[2];
+  const bool bad = !l || (l & 3) || !s || (s & 3) || !p0 || (p0 & 3) || !p1 || (p1 & 3) || !p2 || (p2 & 3);
   return ALB_IN_RANGE(c.chk, CHK_PTR, bad ? 2u : 0u, 1u);
 #else
   (void)c;
@@ -138,8 +144,9 @@ __global__ void __launch_bounds__(kBlock) k_batch_init(TravCtx c) {
     x->lab[i] = kInf;
   for (uint64_t v = (uint64_t)blockIdx.x * kBlock + threadIdx.x; v < n; v += (uint64_t)gridDim.x * kBlock) {
     x->seen[v] = 0u;
-    x->act0[v] = 0ull;
-    x->act1[v] = 0ull;
+    x->act[0][v] = 0u;
+    x->act[1][v] = 0u;
+    x->act[2][v] = 0u;
   }
 }
 
@@ -156,7 +163,7 @@ __global__ void k_batch_seed(TravCtx c) {
     }
     x->lab[(size_t)v * 32u + s] = 0u;
     atomicOr(x->seen + v, bit);
-    if (act_or(x->act0 + v, 0u, bit)) {
+    if (act_or(x->act[0] + v, bit)) {
       const uint32_t slot = atomicAdd(&c.st->fcount[0], 1u);
       if (ALB_IN_RANGE(c.chk, CHK_PUSH, slot, c.n)) c.F0[slot] = v;
     }
@@ -233,7 +240,7 @@ struct BatchWs {
   uint32_t used_workers = 0;   // used by the last call (alb_sync checks them)
   uint32_t* lab = nullptr;
   uint32_t* seen = nullptr;
-  unsigned long long* act = nullptr;
+  uint32_t* act = nullptr;  // 3 x n source masks (BatchAux::act)
   alb::BatchAux* aux = nullptr;
   uint32_t* srcs = nullptr;
   uint32_t cap_srcs = 0;
@@ -296,10 +303,10 @@ static alb_status ensure_batch(alb_graph g, bool group_arrays, uint32_t nsrc, cu
     if (rc != ALB_OK) return rc;
     ALB_CUDA_TRY(cudaMalloc((void**)&b->lab, sizeof(uint32_t) * n * 32u));
     ALB_CUDA_TRY(cudaMalloc((void**)&b->seen, sizeof(uint32_t) * n));
-    ALB_CUDA_TRY(cudaMalloc((void**)&b->act, sizeof(unsigned long long) * n * 2u));
+    ALB_CUDA_TRY(cudaMalloc((void**)&b->act, sizeof(uint32_t) * n * 3u));
     ALB_CUDA_TRY(cudaMalloc((void**)&b->aux, sizeof(BatchAux)));
     // written on the call's stream: the batch kernels queued after it read it
-    BatchAux h{b->lab, b->seen, b->act, b->act + n};
+    BatchAux h{b->lab, b->seen, {b->act, b->act + n, b->act + 2 * n}};
     k_set_aux<<<1, 1, 0, s>>>(b->aux, h);
     ALB_CUDA_TRY(cudaGetLastError());
   }

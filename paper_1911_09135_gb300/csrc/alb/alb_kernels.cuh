@@ -427,6 +427,7 @@ __global__ void __launch_bounds__(kBlock, round_kernel_min_blocks<Op>()) k_inspe
       for (uint32_t i = blockIdx.x * kBlock + tid; i < c.pw; i += gridDim.x * kBlock) other[i] = 0u;
     }
   }
+  if constexpr (Op::kBatch) Op::round_start(a, r);  // multi-source operators' per-round state
 
   // Tiles of kBlock frontier entries, taken dynamically. Tile t is made of the 32-entry chunks
   // t, t + T, ..., t + 7T (T tiles; warp w reads chunk t + wT, coalesced): vertices found

@@ -54,9 +54,9 @@ EDGES_PER_CTA = 1 << 17       # serving grids: one CTA per this many edges, at m
 
 # Device bytes per vertex of the library's workspaces (include/alb.h): the round workspace of a
 # handle (two frontiers, huge worklist and prefix, two push bitmaps) and the multi-source batch
-# workspace (32 labels, a seen mask and two round-tagged masks per vertex).
+# workspace (32 labels, a seen mask and three round masks per vertex).
 ROUND_WS_PER_VERTEX = 17
-BATCH_WS_PER_VERTEX = 148
+BATCH_WS_PER_VERTEX = 144
 
 
 def result_bytes(n: int, kind: str) -> int:

@@ -223,7 +223,7 @@ def test_batch_bytes_count_only_what_the_slot_lacks():
     gr = srv.graphs[0]
     s = gr.slots[0]
     n = g.n
-    assert gr.batch_bytes(s, 3, 0, 0) == 4 * 32 * n + 148 * n
+    assert gr.batch_bytes(s, 3, 0, 0) == 4 * 32 * n + serve.BATCH_WS_PER_VERTEX * n
     assert gr.batch_bytes(s, 0, 0, 2) == 4 * n
     s.ensure(["bfs"], 0)
     assert gr.batch_bytes(s, 3, 0, 0) == 0
