@@ -86,15 +86,6 @@ struct MsBfsOp {
 struct MsSsspOp {
   static constexpr bool kBatch = true;
   static constexpr bool kW = true;
-  // An edge costs one relaxation per active source, so a vertex is binned (Algorithm 1: huge,
-  // CTA, warp, thread) by degree x active sources: a vertex of a few hundred edges active for 32
-  // sources is as much work as a hub of ten thousand edges active for one, and expanded by one
-  // warp it kept a single CTA busy long after the rest of the grid had finished its round.
-  static constexpr bool kWeighted = true;
-  __device__ static uint32_t work(const OpArgs& a, uint32_t v, uint32_t deg) {
-    const uint64_t w = (uint64_t)deg * (uint64_t)__popc(act_mask(static_cast<const BatchAux*>(a.aux), a.next - 1u, v));
-    return w > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)w;
-  }
   __device__ static void round_start(const OpArgs& a, uint32_t r) {
     act_clear(static_cast<const BatchAux*>(a.aux), r, a.n);
   }

@@ -153,13 +153,6 @@ struct uses_push_bitmap { static constexpr bool value = false; };
 template <class Op>
 struct uses_push_bitmap<Op, decltype(void(Op::kPushBitmap))> { static constexpr bool value = Op::kPushBitmap; };
 
-// Work of an active vertex for the binning of Algorithm 1: its degree, or, for an operator whose
-// per-edge cost varies by vertex (it defines work()), that operator's measure.
-template <class Op, class = void>
-struct weighs_work { static constexpr bool value = false; };
-template <class Op>
-struct weighs_work<Op, decltype(void(Op::kWeighted))> { static constexpr bool value = Op::kWeighted; };
-
 template <class Op, class = void>
 struct aggregates { static constexpr bool value = false; };
 template <class Op>
@@ -461,11 +454,9 @@ __global__ void __launch_bounds__(kBlock, round_kernel_min_blocks<Op>()) k_inspe
       deg = c.off[v + 1] - beg;
       sv = Op::sval(a, v);
     }
-    uint32_t wdeg = deg;
-    if constexpr (weighs_work<Op>::value) wdeg = valid ? Op::work(a, v, deg) : 0u;
-    const bool huge = valid && wdeg >= c.threshold;
-    const bool cta = valid && !huge && wdeg >= c.cta_min;
-    const bool wrp = valid && !huge && !cta && wdeg >= c.warp_min;
+    const bool huge = valid && deg >= c.threshold;
+    const bool cta = valid && !huge && deg >= c.cta_min;
+    const bool wrp = valid && !huge && !cta && deg >= c.warp_min;
     const uint32_t sdeg = (valid && !huge && !cta && !wrp) ? deg : 0u;
     if (valid && !huge) twc_edges += deg;
     hub_append(huge, v, deg, c.hub_v, c.hub_p, &st->hub_packed, c.n + 1u, c.chk);
