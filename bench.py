@@ -423,7 +423,7 @@ def gpu_arm(args, dist):
         for a in apps:
             p, _ = step.G.autotune(a, tsrc, reps=2)
             tuned[a] = {"hub_threshold": p.hub_threshold, "twc_cta_min": p.twc_cta_min,
-                        "twc_warp_min": p.twc_warp_min}
+                        "twc_warp_min": p.twc_warp_min, "block_size": p.block_size}
     if args.exec_mode == "host":
         for a in apps:
             step.G.set_app_params(a, exec_mode=1)
@@ -769,7 +769,7 @@ def batch_arm(args, dist):
             res[app] = {"queries": 128, "ms_plain": round(ms_plain, 3), "ms_batched": round(ms_batch, 3),
                         "speedup": round(ms_plain / ms_batch, 2),
                         "autotuned": {"hub_threshold": tuned.hub_threshold, "twc_cta_min": tuned.twc_cta_min,
-                                      "twc_warp_min": tuned.twc_warp_min},
+                                      "twc_warp_min": tuned.twc_warp_min, "block_size": tuned.block_size},
                         "batched_hub_threshold": t_best,
                         "queries_per_s_batched": round(128 / (ms_batch * 1e-3), 1)}
         G.close()

@@ -105,6 +105,10 @@ typedef struct {
                               * 0 = off (default) */
   uint32_t profile;        /* 1: time every kernel launch with CUDA events (host loop only) */
   uint32_t cta_stats;      /* 1: count the edges each CTA expands (alb_get_cta_loads) */
+  uint32_t block_size;     /* threads per CTA of the round kernels (inspection + TWC, LB kernel):
+                            * 128, 256 (default; the paper's 2^8, Sec. 5.1) or 512; 0 = 256.
+                            * The LB kernel's thread count, and so the default threshold, follows
+                            * it. PageRank's kernels keep 256. */
 } alb_params;
 
 /* Counters of the last completed call on a handle. */
@@ -242,8 +246,8 @@ alb_status alb_get_app_params(alb_graph g, alb_app app, alb_params* p);
  * (Sec. 4.1 "Threshold": the best threshold depends on the hardware; Sec. 5.1 finds a wide
  * flat range). Coordinate search: the threshold over {threads of the LB kernel, 2^8, 2^10, ...,
  * 2^20, never huge}, then twc_cta_min in {128, 256, 512, 1024} x twc_warp_min in {16, 32, 64}
- * at the best threshold; each setting is timed as the mean of `reps` calls after one warm-up
- * call. The fastest setting is applied to that application (alb_set_app_params) and returned
+ * at the best threshold, then block_size in {128, 256, 512} (not for PageRank); each setting is
+ * timed as the mean of `reps` calls after one warm-up call. The fastest setting is applied to that application (alb_set_app_params) and returned
  * in *best (may be NULL) with
  * its time in *best_ms (may be NULL). src is used by bfs and sssp. Synchronises `stream`.
  * Results of every setting are identical (only the schedule changes). */

@@ -60,6 +60,7 @@ class alb_params(ctypes.Structure):
         ("l2_persist_fraction", ctypes.c_float),
         ("profile", ctypes.c_uint32),
         ("cta_stats", ctypes.c_uint32),
+        ("block_size", ctypes.c_uint32),
     ]
 
 

@@ -352,20 +352,20 @@ static BatchCfg batch_cfg(alb_graph g, BatchKind kind) {
   switch (kind) {
     case BK_MS_BFS:
       k.init = (void*)k_batch_init; k.seed = (void*)k_batch_seed;
-      k.insp = (void*)k_inspect<MsBfsOp>; k.lb = (void*)k_lb<MsBfsOp, false>;
+      k.insp = inspect_for<MsBfsOp>(g->block); k.lb = lb_for<MsBfsOp>(g->block);
       break;
     case BK_MS_SSSP:
       k.init = (void*)k_batch_init; k.seed = (void*)k_batch_seed;
-      k.insp = (void*)k_inspect<MsSsspOp>; k.lb = (void*)k_lb<MsSsspOp, false>;
+      k.insp = inspect_for<MsSsspOp>(g->block); k.lb = lb_for<MsSsspOp>(g->block);
       break;
     case BK_MULTI_BFS:
       k.init = (void*)k_multi_init<APP_BFS>; k.seed = (void*)k_multi_seed;
-      k.insp = (void*)k_inspect<BfsOp>; k.lb = (void*)k_lb<BfsOp, false>;
+      k.insp = inspect_for<BfsOp>(g->block); k.lb = lb_for<BfsOp>(g->block);
       k.seed_grid = g->blocks; k.seed_block = kBlock;
       break;
     default:
       k.init = (void*)k_multi_init<APP_SSSP>; k.seed = (void*)k_multi_seed;
-      k.insp = (void*)k_inspect<SsspOp>; k.lb = (void*)k_lb<SsspOp, false>;
+      k.insp = inspect_for<SsspOp>(g->block); k.lb = lb_for<SsspOp>(g->block);
       k.seed_grid = g->blocks; k.seed_block = kBlock;
       break;
   }
@@ -374,12 +374,12 @@ static BatchCfg batch_cfg(alb_graph g, BatchKind kind) {
   k.threshold = g->threshold;
   if (!g->params.grid_blocks) {
     int bi = 0, bl = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bi, k.insp, kBlock, 0) == cudaSuccess && bi > 0)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bi, k.insp, (int)g->block, 0) == cudaSuccess && bi > 0)
       k.ib = (uint32_t)g->num_sms * (uint32_t)bi;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, k.lb, kBlock, 0) == cudaSuccess && bl > 0)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, k.lb, (int)g->block, 0) == cudaSuccess && bl > 0)
       k.lbb = (uint32_t)g->num_sms * (uint32_t)bl;
     cudaGetLastError();
-    if (g->params.hub_threshold < 0) k.threshold = k.lbb * (uint32_t)kBlock;
+    if (g->params.hub_threshold < 0) k.threshold = k.lbb * g->block;
   }
   return k;
 }
@@ -417,14 +417,14 @@ static alb_status build_batch_graph(alb_graph g, BatchKind kind) {
   wp.conditional.size = 1;
   if (cudaGraphAddNode(&n_while, G, &n_seed, nullptr, 1, &wp) != cudaSuccess) return fail(ALB_ERR_CUDA);
   cudaGraph_t body = wp.conditional.phGraph_out[0];
-  if ((rc = add_node(&n_insp, body, nullptr, 0, insp, ib, kBlock, &c)) != ALB_OK) return fail(rc);
+  if ((rc = add_node(&n_insp, body, nullptr, 0, insp, ib, g->block, &c)) != ALB_OK) return fail(rc);
   cudaGraphNodeParams ip{};
   ip.type = cudaGraphNodeTypeConditional;
   ip.conditional.handle = hi;
   ip.conditional.type = cudaGraphCondTypeIf;
   ip.conditional.size = 1;
   if (cudaGraphAddNode(&n_if, body, &n_insp, nullptr, 1, &ip) != cudaSuccess) return fail(ALB_ERR_CUDA);
-  if ((rc = add_node(&n_lb, ip.conditional.phGraph_out[0], nullptr, 0, lb, lbb, kBlock, &c)) != ALB_OK)
+  if ((rc = add_node(&n_lb, ip.conditional.phGraph_out[0], nullptr, 0, lb, lbb, g->block, &c)) != ALB_OK)
     return fail(rc);
   if (kind == BK_MS_BFS || kind == BK_MS_SSSP) {
     if ((rc = add_node(&n_out, G, &n_while, 1, (void*)k_batch_out, g->blocks, kBlock, &c)) != ALB_OK)
@@ -483,11 +483,11 @@ static alb_status batch_host_loop(alb_graph g, BatchKind kind, cudaStream_t s) {
   if ((rc = launch(k.init, g->blocks, kBlock, nullptr, nullptr)) != ALB_OK) return rc;
   if ((rc = launch(k.seed, k.seed_grid, k.seed_block, nullptr, nullptr)) != ALB_OK) return rc;
   for (;;) {
-    if ((rc = launch(k.insp, k.ib, kBlock, &g->stats.ms_inspect, &g->stats.n_inspect)) != ALB_OK) return rc;
+    if ((rc = launch(k.insp, k.ib, g->block, &g->stats.ms_inspect, &g->stats.n_inspect)) != ALB_OK) return rc;
     ALB_CUDA_TRY(cudaMemcpyAsync(g->h_st, g->st, sizeof(RoundState), cudaMemcpyDeviceToHost, s));
     ALB_CUDA_TRY(cudaStreamSynchronize(s));
     if (g->h_st->hub_packed >> 32) {
-      if ((rc = launch(k.lb, k.lbb, kBlock, &g->stats.ms_lb, &g->stats.n_lb)) != ALB_OK) return rc;
+      if ((rc = launch(k.lb, k.lbb, g->block, &g->stats.ms_lb, &g->stats.n_lb)) != ALB_OK) return rc;
       ALB_CUDA_TRY(cudaMemcpyAsync(g->h_st, g->st, sizeof(RoundState), cudaMemcpyDeviceToHost, s));
       ALB_CUDA_TRY(cudaStreamSynchronize(s));
     }

@@ -121,17 +121,18 @@ static alb_status alloc_workspace(alb_graph g) {
 }
 
 static void apply_launch_config(alb_graph g, int app, const alb_params& p) {
-  uint32_t occ_i = 1, occ_l = 1;
-  occupancy(&occ_i, &occ_l);
   alb_graph_s::AppCfg& c = g->cfg[app];
   c.p = p;
+  c.block = p.block_size ? p.block_size : (uint32_t)kBlock;
+  uint32_t occ_i = 1, occ_l = 1;
+  occupancy(c.block, &occ_i, &occ_l);
   if (p.grid_blocks) {
     c.blocks = c.lb_blocks = p.grid_blocks;
   } else {
     c.blocks = (uint32_t)g->num_sms * occ_i;
     c.lb_blocks = (uint32_t)g->num_sms * occ_l;
   }
-  if (p.hub_threshold < 0) c.threshold = c.lb_blocks * (uint32_t)kBlock;
+  if (p.hub_threshold < 0) c.threshold = c.lb_blocks * c.block;
   else c.threshold = p.hub_threshold > 0xFFFFFFFFll ? 0xFFFFFFFFu : (uint32_t)p.hub_threshold;
 }
 
@@ -141,6 +142,7 @@ void select_cfg(alb_graph g, int app) {
   g->blocks = c.blocks;
   g->lb_blocks = c.lb_blocks;
   g->threshold = c.threshold;
+  g->block = c.block;
 }
 
 alb_status reset_cta_loads(alb_graph g, cudaStream_t s, uint32_t min_need) {
@@ -249,11 +251,13 @@ alb_status alb_default_params(alb_params* p) {
   p->max_rounds = 0;
   p->l2_persist_fraction = 0.f;
   p->profile = 0;
+  p->block_size = (uint32_t)kBlock;
   return ALB_OK;
 }
 
 static bool params_valid(const alb_params* p) {
   if (p->distribution > 1 || p->exec_mode > 1 || p->profile > 1 || p->cta_stats > 1) return false;
+  if (p->block_size != 0 && p->block_size != 128 && p->block_size != 256 && p->block_size != 512) return false;
   if (p->twc_warp_min > p->twc_cta_min) return false;
   if (p->grid_blocks > (1u << 20)) return false;
   if (!(p->l2_persist_fraction >= 0.f && p->l2_persist_fraction <= 1.f)) return false;
@@ -469,9 +473,9 @@ alb_status alb_get_stats(alb_graph g, alb_stats* out) {
   ALB_CUDA_TRY(cudaStreamSynchronize(g->last_stream));
   alb_stats s = g->stats;
   s.hub_threshold = g->threshold;
-  s.lb_threads = g->lb_blocks * (uint32_t)kBlock;
+  s.lb_threads = g->lb_blocks * g->block;
   s.grid_blocks = g->blocks;
-  s.block_size = (uint32_t)kBlock;
+  s.block_size = g->block;
   if (g->last_kind == 0) {
     ALB_CUDA_TRY(cudaMemcpy(g->h_st, g->st, sizeof(RoundState), cudaMemcpyDeviceToHost));
     const RoundState& h = *g->h_st;

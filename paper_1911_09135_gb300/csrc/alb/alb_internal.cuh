@@ -118,13 +118,14 @@ struct alb_graph_s {
   // configuration of the application being called (select_cfg copies it in)
   struct AppCfg {
     alb_params p{};
-    uint32_t blocks = 0, lb_blocks = 0, threshold = 0;
+    uint32_t blocks = 0, lb_blocks = 0, threshold = 0, block = alb::kBlock;
   } cfg[5];
   alb_params params{};
   int num_sms = 0;
   uint32_t blocks = 0;        // CTAs of the inspection / init kernels (persistent grid)
   uint32_t lb_blocks = 0;     // CTAs of the LB kernel (its threads are the default threshold)
   uint32_t threshold = 0;     // effective huge threshold
+  uint32_t block = alb::kBlock;  // threads per CTA of the round kernels
 
   // traversal workspace
   uint32_t* F0 = nullptr;
@@ -190,7 +191,8 @@ alb_status launch_lb_trace(alb_graph g, const uint32_t* d_work, const uint32_t* 
 alb_status launch_inspect_only(alb_graph g, const uint32_t* d_wl, uint32_t nf, uint8_t* d_bin,
                                uint32_t* d_work, uint32_t* d_prefix, uint32_t* d_counts,
                                cudaStream_t s);
-void occupancy(uint32_t* inspect_per_sm, uint32_t* lb_per_sm);
+// Resident CTAs per SM of the round kernels built for CTA size B (the least over the apps).
+void occupancy(uint32_t B, uint32_t* inspect_per_sm, uint32_t* lb_per_sm);
 alb_status pr_stats(alb_graph g, alb_stats* out);
 alb_status batch_stats(alb_graph g, alb_stats* out);
 alb_status batch_sync_workers(alb_graph g);  // status of the worker clones of the last batch call

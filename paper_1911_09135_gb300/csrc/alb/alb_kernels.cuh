@@ -169,7 +169,7 @@ constexpr uint32_t kHotBits = 10;
 constexpr uint32_t kHotSlots = 1u << kHotBits;
 constexpr uint32_t kHotProbe = 4;
 constexpr uint32_t kHotDeg = 1u << 16;
-static_assert(kHotSlots % kBlock == 0, "the table flush loop needs a uniform trip count");
+static_assert(kHotSlots % 512 == 0, "the table flush loop needs a uniform trip count at every CTA size");
 
 __device__ __forceinline__ bool hot_add(uint32_t* key, uint32_t* cnt, uint32_t v, uint32_t n) {
   uint32_t s = (v * 2654435761u) >> (32 - kHotBits);
@@ -192,7 +192,9 @@ __device__ __forceinline__ bool hot_add(uint32_t* key, uint32_t* cnt, uint32_t v
 // atomics serialise in L2, so the TWC kernel collects a tile's pushes in shared memory (one
 // shared atomic per warp and step) and moves them to the frontier with one global atomic per
 // tile. Pushes that do not fit in the buffer go to the frontier directly.
-constexpr uint32_t kPushBuf = 2048;
+// Staging entries per CTA: 2048, or one LB step of the CTA (B threads x 8 positions) if larger.
+template <int B>
+constexpr uint32_t kPushBufOf = (uint32_t)B * 8u > 2048u ? (uint32_t)B * 8u : 2048u;
 
 struct PushSink {
   uint32_t* Fn;      // next frontier
@@ -200,7 +202,8 @@ struct PushSink {
   uint32_t cap;      // its capacity (n)
   uint32_t* chk;
   uint32_t* sbuf;    // CTA staging buffer (shared memory), or null: push to Fn directly
-  uint32_t* sn;      // entries claimed in it (may exceed kPushBuf; the excess went to Fn)
+  uint32_t* sn;      // entries claimed in it (may exceed scap; the excess went to Fn)
+  uint32_t scap;     // entries of sbuf
 };
 
 // Warp-aggregated push of up to U values per lane (v[u] where pred[u]); every lane of the warp
@@ -221,16 +224,16 @@ __device__ __forceinline__ void push_n(const bool (&pred)[U], const uint32_t (&v
   if (lane_id() == 0u) {
     base = atomicAdd(k.sn, total);
     const uint32_t end = base + total;
-    if (end > kPushBuf) gbase = atomicAdd(k.ncount, end - (base > kPushBuf ? base : kPushBuf));
+    if (end > k.scap) gbase = atomicAdd(k.ncount, end - (base > k.scap ? base : k.scap));
   }
   base = __shfl_sync(kFull, base, 0);
   gbase = __shfl_sync(kFull, gbase, 0);
-  const uint32_t over0 = base > kPushBuf ? base : kPushBuf;  // first position sent to Fn
+  const uint32_t over0 = base > k.scap ? base : k.scap;  // first position sent to Fn
   uint32_t pos = base + incl - cnt;
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     if (pred[u]) {
-      if (pos < kPushBuf) {
+      if (pos < k.scap) {
         k.sbuf[pos] = v[u];
       } else {
         const uint32_t g = gbase + (pos - over0);
@@ -244,7 +247,7 @@ __device__ __forceinline__ void push_n(const bool (&pred)[U], const uint32_t (&v
 // Move the staged pushes to the frontier: one global atomic, coalesced stores. Called by every
 // thread of the CTA after a barrier that follows the tile's last push.
 __device__ __forceinline__ void push_flush(const PushSink& k, uint32_t* s_base) {
-  const uint32_t nb = *k.sn < kPushBuf ? *k.sn : kPushBuf;
+  const uint32_t nb = *k.sn < k.scap ? *k.sn : k.scap;
   if (nb == 0u) return;  // CTA-uniform
   if (threadIdx.x == 0) *s_base = atomicAdd(k.ncount, nb);
   __syncthreads();
@@ -375,8 +378,11 @@ static __device__ __forceinline__ void hub_append(bool huge, uint32_t v, uint32_
 // latency chain: +8 % over bfs, sssp, cc and k-core on rmat24-hubs); 4 for the multi-source
 // operators, which hold a row of labels per edge (5 spilled up to 272 bytes; with no minimum,
 // ptxas gave them up to 118 registers and 2 CTAs per SM, 1.4x slower batches).
-template <class Op>
-constexpr int round_kernel_min_blocks() { return Op::kBatch ? 4 : 5; }
+template <class Op, int B>
+constexpr int round_kernel_min_blocks() { return (Op::kBatch ? 4 : 5) * kBlock / B; }
+
+// CTA sizes the round kernels are built for (alb_params.block_size); kBlock is the default.
+constexpr int kBlockSizes[] = {128, 256, 512};
 
 // Edges relaxed per thread per step (memory requests a thread keeps in flight), per bin.
 constexpr int kUCta = 8;     // CTA bin
@@ -385,17 +391,18 @@ constexpr int kUThread = 4;  // thread bin (fine-grained gather)
 constexpr int kULb = 8;      // LB kernel
 constexpr int kUMs = 8;      // multi-source operators (every bin and the LB kernel)
 
-template <class Op>
-__global__ void __launch_bounds__(kBlock, round_kernel_min_blocks<Op>()) k_inspect(TravCtx c) {
-  __shared__ uint32_t s_cb[kBlock], s_cd[kBlock], s_cv[kBlock];       // CTA bin
-  __shared__ uint32_t s_wb[kBlock], s_wd[kBlock], s_wv[kBlock];       // warp bin
-  __shared__ uint32_t s_scan[kBlock + 1], s_sb[kBlock], s_sv[kBlock];  // thread bin
-  __shared__ uint32_t s_warp[kWarps + 1];
+template <class Op, int B>
+__global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_inspect(TravCtx c) {
+  constexpr int kNW = B / 32;  // warps of the CTA
+  __shared__ uint32_t s_cb[B], s_cd[B], s_cv[B];       // CTA bin
+  __shared__ uint32_t s_wb[B], s_wd[B], s_wv[B];       // warp bin
+  __shared__ uint32_t s_scan[B + 1], s_sb[B], s_sv[B];  // thread bin
+  __shared__ uint32_t s_warp[kNW + 1];
   __shared__ uint32_t s_ncta, s_nwrp, s_tile;
   constexpr int UC = Op::kBatch ? kUMs : kUCta;  // edges in flight per thread, per bin
   constexpr int UW = Op::kBatch ? kUMs : kUWarp;
   constexpr int UT = Op::kBatch ? (kUMs < kUThread ? kUMs : kUThread) : kUThread;
-  __shared__ uint32_t s_push[kPushBuf];  // the tile's pushes (PushSink)
+  __shared__ uint32_t s_push[kPushBufOf<B>];  // the tile's pushes (PushSink)
   __shared__ uint32_t s_npush, s_pbase;
   constexpr bool kHot = aggregates<Op>::value;
   constexpr uint32_t kHotN = kHot ? kHotSlots : 1u;
@@ -403,7 +410,7 @@ __global__ void __launch_bounds__(kBlock, round_kernel_min_blocks<Op>()) k_inspe
   uint32_t* hk = kHot ? s_hkey : nullptr;
   uint32_t* hc = kHot ? s_hcnt : nullptr;
   if constexpr (kHot) {
-    for (uint32_t i = threadIdx.x; i < kHotSlots; i += kBlock) { s_hkey[i] = kInf; s_hcnt[i] = 0u; }
+    for (uint32_t i = threadIdx.x; i < kHotSlots; i += B) { s_hkey[i] = kInf; s_hcnt[i] = 0u; }
   }  // visible after the tile loop's first barrier
 
   RoundState* st = c.st;
@@ -419,21 +426,21 @@ __global__ void __launch_bounds__(kBlock, round_kernel_min_blocks<Op>()) k_inspe
   const OpArgs a{ca->lab, c.pushed ? c.pushed + (size_t)cur * c.pw : nullptr, r + 1u, ca->k, ca->aux, c.n, c.chk};
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   unsigned long long twc_edges = 0ull;
-  const PushSink sink{Fn, ncount, c.n, c.chk, s_push, &s_npush};
+  const PushSink sink{Fn, ncount, c.n, c.chk, s_push, &s_npush, kPushBufOf<B>};
   if constexpr (uses_push_bitmap<Op>::value) {
     // the other bitmap (last round's) is cleared for the next round
     if (c.pushed) {
       uint32_t* other = c.pushed + (size_t)(cur ^ 1u) * c.pw;
-      for (uint32_t i = blockIdx.x * kBlock + tid; i < c.pw; i += gridDim.x * kBlock) other[i] = 0u;
+      for (uint32_t i = blockIdx.x * B + tid; i < c.pw; i += gridDim.x * B) other[i] = 0u;
     }
   }
   if constexpr (Op::kBatch) Op::round_start(a, r);  // multi-source operators' per-round state
 
-  // Tiles of kBlock frontier entries, taken dynamically. Tile t is made of the 32-entry chunks
+  // Tiles of B frontier entries, taken dynamically. Tile t is made of the 32-entry chunks
   // t, t + T, ..., t + 7T (T tiles; warp w reads chunk t + wT, coalesced): vertices found
   // together (often of similar degree) spread over many tiles, so no tile holds a run of
   // CTA-bin vertices that would leave its CTA the last one running.
-  const uint32_t ntiles = (uint32_t)(((uint64_t)nf + kBlock - 1) / kBlock);
+  const uint32_t ntiles = (uint32_t)(((uint64_t)nf + B - 1) / B);
   for (;;) {
     if (tid == 0) {
       s_tile = atomicAdd(&st->tile_next, 1u);
@@ -469,23 +476,23 @@ __global__ void __launch_bounds__(kBlock, round_kernel_min_blocks<Op>()) k_inspe
       s_wb[s] = beg; s_wd[s] = deg; s_wv[s] = sv;
     }
     uint32_t stotal;
-    const uint32_t ex = block_exclusive_scan<kBlock>(sdeg, s_warp, &stotal);
+    const uint32_t ex = block_exclusive_scan<B>(sdeg, s_warp, &stotal);
     s_scan[tid] = ex;
     s_sb[tid] = beg;
     s_sv[tid] = sv;
-    if (tid == 0) s_scan[kBlock] = stotal;
+    if (tid == 0) s_scan[B] = stotal;
     __syncthreads();
 
     // CTA bin: the whole CTA expands one vertex at a time.
     const uint32_t ncta = s_ncta;
     for (uint32_t j = 0; j < ncta; ++j) {
       const uint32_t b = s_cb[j], d = s_cd[j], svj = s_cv[j];
-      for (uint32_t e0 = 0; e0 < d; e0 += kBlock * UC) {
+      for (uint32_t e0 = 0; e0 < d; e0 += B * UC) {
         uint32_t e[UC], s4[UC];
         bool ok[UC];
 #pragma unroll
         for (int u = 0; u < UC; ++u) {
-          const uint32_t q = e0 + u * kBlock + tid;
+          const uint32_t q = e0 + u * B + tid;
           ok[u] = q < d; e[u] = b + q; s4[u] = svj;
         }
         relax<Op, UC>(c, a, e, ok, s4, sink, hk, hc);
@@ -493,7 +500,7 @@ __global__ void __launch_bounds__(kBlock, round_kernel_min_blocks<Op>()) k_inspe
     }
     // Warp bin: one warp per vertex.
     const uint32_t nw = s_nwrp;
-    for (uint32_t j = warp; j < nw; j += kWarps) {
+    for (uint32_t j = warp; j < nw; j += kNW) {
       const uint32_t b = s_wb[j], d = s_wd[j], svj = s_wv[j];
       for (uint32_t e0 = 0; e0 < d; e0 += 32 * UW) {
         uint32_t e[UW], s4[UW];
@@ -508,18 +515,18 @@ __global__ void __launch_bounds__(kBlock, round_kernel_min_blocks<Op>()) k_inspe
     }
     // Thread bin: the small vertices' edges, gathered over the whole CTA
     // (consecutive threads take consecutive edges of the concatenated lists).
-    const uint32_t S = s_scan[kBlock];
+    const uint32_t S = s_scan[B];
     uint32_t owner = 0u;
-    for (uint32_t q0 = 0; q0 < S; q0 += kBlock * UT) {
+    for (uint32_t q0 = 0; q0 < S; q0 += B * UT) {
       uint32_t e[UT], s2[UT];
       bool ok[UT];
 #pragma unroll
       for (int u = 0; u < UT; ++u) {
-        const uint32_t q = q0 + u * kBlock + tid;
+        const uint32_t q = q0 + u * B + tid;
         ok[u] = q < S;
         e[u] = 0u; s2[u] = 0u;
         if (ok[u]) {
-          owner = upper_search(s_scan, owner, kBlock, q);
+          owner = upper_search(s_scan, owner, B, q);
           e[u] = s_sb[owner] + (q - s_scan[owner]);
           s2[u] = s_sv[owner];
         }
@@ -532,7 +539,7 @@ __global__ void __launch_bounds__(kBlock, round_kernel_min_blocks<Op>()) k_inspe
   if constexpr (kHot) {
     // apply the CTA's pending counts: one atomic per target; the one that crosses k pushes it
     __syncthreads();
-    for (uint32_t i = tid; i < kHotSlots; i += kBlock) {  // same trip count in every thread
+    for (uint32_t i = tid; i < kHotSlots; i += B) {  // same trip count in every thread
       const uint32_t v = s_hkey[i];
       const bool push = v != kInf && ALB_IN_RANGE(c.chk, CHK_DST, v, c.n) && Op::commit_n(a, v, s_hcnt[i]);
       warp_append(push, v, Fn, ncount, c.n, c.chk);
@@ -559,14 +566,14 @@ __global__ void __launch_bounds__(kBlock, round_kernel_min_blocks<Op>()) k_inspe
 
 struct TraceOp {};
 
-template <class Op, bool kTrace>
-__global__ void __launch_bounds__(kBlock, round_kernel_min_blocks<Op>()) k_lb(TravCtx c) {
+template <class Op, bool kTrace, int B>
+__global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_lb(TravCtx c) {
   constexpr int kStage = kHubSmem;
   __shared__ uint32_t s_p[kStage];
   __shared__ uint32_t s_base[kStage];
   __shared__ uint32_t s_val[kStage];
   __shared__ uint32_t s_src[kTrace ? kStage : 1];
-  __shared__ uint32_t s_push[kTrace ? 1 : kPushBuf];  // one step's pushes (PushSink)
+  __shared__ uint32_t s_push[kTrace ? 1 : kPushBufOf<B>];  // one step's pushes (PushSink)
   __shared__ uint32_t s_npush, s_pbase;
 
   RoundState* st = c.st;
@@ -585,15 +592,15 @@ __global__ void __launch_bounds__(kBlock, round_kernel_min_blocks<Op>()) k_lb(Tr
   const CallArgs* ca = c.args;
   const OpArgs a{ca->lab, c.pushed ? c.pushed + (size_t)cur * c.pw : nullptr, r + 1u, ca->k, ca->aux, c.n, c.chk};
   const uint32_t tid = threadIdx.x, lane = tid & 31u;
-  // a step of the CTA is kBlock x U positions, at most one push each: the buffer never overflows
-  static_assert(kTrace || kBlock * (Op::kBatch ? kUMs : kULb) <= kPushBuf,
+  // a step of the CTA is B x U positions, at most one push each: the buffer never overflows
+  static_assert(kTrace || B * (Op::kBatch ? kUMs : kULb) <= kPushBufOf<B>,
                 "one LB step's pushes must fit the CTA buffer");
-  const PushSink sink{Fn, ncount, c.n, c.chk, kTrace ? nullptr : s_push, &s_npush};
+  const PushSink sink{Fn, ncount, c.n, c.chk, kTrace ? nullptr : s_push, &s_npush, kPushBufOf<B>};
   if (threadIdx.x == 0) s_npush = 0u;
 
   const bool staged = nh <= (uint32_t)kStage;
   if (staged) {
-    for (uint32_t j = tid; j < nh; j += kBlock) {
+    for (uint32_t j = tid; j < nh; j += B) {
       uint32_t u = c.hub_v[j];
       const uint32_t p = c.hub_p[j];
       if (!ALB_IN_RANGE(c.chk, CHK_FRONTIER, u, c.n)) u = 0u;
@@ -628,8 +635,8 @@ __global__ void __launch_bounds__(kBlock, round_kernel_min_blocks<Op>()) k_lb(Tr
     }
   };
 
-  const uint64_t p = (uint64_t)gridDim.x * kBlock;
-  const uint64_t gt = (uint64_t)blockIdx.x * kBlock + tid;
+  const uint64_t p = (uint64_t)gridDim.x * B;
+  const uint64_t gt = (uint64_t)blockIdx.x * B + tid;
   constexpr int U = Op::kBatch ? kUMs : kULb;
   unsigned long long lb_edges = 0ull;  // positions this thread processed (cta_stats)
   auto process = [&](const uint64_t (&k)[U], const bool (&ok)[U]) {
@@ -667,7 +674,7 @@ __global__ void __launch_bounds__(kBlock, round_kernel_min_blocks<Op>()) k_lb(Tr
   };
   if (c.distribution == 0u) {
     // cyclic: thread gt takes positions gt, gt + p, gt + 2p, ... (Sec. 4.1)
-    const uint64_t cta0 = (uint64_t)blockIdx.x * kBlock;
+    const uint64_t cta0 = (uint64_t)blockIdx.x * B;
     for (uint64_t c0 = cta0; c0 < e; c0 += p * U) {  // CTA-uniform
       const uint64_t k0 = c0 + (gt - cta0) - lane;
       uint64_t k[U];
@@ -745,5 +752,23 @@ static __global__ void k_kcore_finish(const CallArgs* ca, uint32_t n) {
 }
 
 static __global__ void k_set_args(CallArgs* dst, CallArgs v) { *dst = v; }
+
+// The round kernels of operator Op built for CTA size B (128, 256 or 512; anything else: kBlock).
+template <class Op>
+static inline void* inspect_for(uint32_t B) {
+  switch (B) {
+    case 128: return (void*)k_inspect<Op, 128>;
+    case 512: return (void*)k_inspect<Op, 512>;
+    default: return (void*)k_inspect<Op, kBlock>;
+  }
+}
+template <class Op, bool kTrace = false>
+static inline void* lb_for(uint32_t B) {
+  switch (B) {
+    case 128: return (void*)k_lb<Op, kTrace, 128>;
+    case 512: return (void*)k_lb<Op, kTrace, 512>;
+    default: return (void*)k_lb<Op, kTrace, kBlock>;
+  }
+}
 
 }  // namespace alb

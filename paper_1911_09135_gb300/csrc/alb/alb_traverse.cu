@@ -51,22 +51,22 @@ __global__ void k_setup_trace(RoundState* st, const uint32_t* prefix, uint32_t n
 
 // ---------------------------------------------------------------- host side
 
-static void* inspect_fn(App app) {
+static void* inspect_fn(App app, uint32_t B) {
   switch (app) {
-    case APP_BFS: return (void*)k_inspect<BfsOp>;
-    case APP_SSSP: return (void*)k_inspect<SsspOp>;
-    case APP_CC: return (void*)k_inspect<CcOp>;
-    case APP_KCORE: return (void*)k_inspect<KcoreOp>;
+    case APP_BFS: return inspect_for<BfsOp>(B);
+    case APP_SSSP: return inspect_for<SsspOp>(B);
+    case APP_CC: return inspect_for<CcOp>(B);
+    case APP_KCORE: return inspect_for<KcoreOp>(B);
     default: return nullptr;
   }
 }
-static void* lb_fn(App app) {
+static void* lb_fn(App app, uint32_t B) {
   switch (app) {
-    case APP_BFS: return (void*)k_lb<BfsOp, false>;
-    case APP_SSSP: return (void*)k_lb<SsspOp, false>;
-    case APP_CC: return (void*)k_lb<CcOp, false>;
-    case APP_KCORE: return (void*)k_lb<KcoreOp, false>;
-    case APP_TRACE: return (void*)k_lb<BfsOp, true>;
+    case APP_BFS: return lb_for<BfsOp>(B);
+    case APP_SSSP: return lb_for<SsspOp>(B);
+    case APP_CC: return lb_for<CcOp>(B);
+    case APP_KCORE: return lb_for<KcoreOp>(B);
+    case APP_TRACE: return (void*)k_lb<BfsOp, true, kBlock>;
     default: return nullptr;
   }
 }
@@ -81,13 +81,13 @@ static void* init_fn(App app) {
 }
 
 // Resident CTAs per SM of the round kernels (the grid is persistent).
-void occupancy(uint32_t* inspect_per_sm, uint32_t* lb_per_sm) {
+void occupancy(uint32_t B, uint32_t* inspect_per_sm, uint32_t* lb_per_sm) {
   int mi = 1 << 30, ml = 1 << 30;
   for (int a = APP_BFS; a <= APP_KCORE; ++a) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, inspect_fn((App)a), kBlock, 0) == cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, inspect_fn((App)a, B), (int)B, 0) == cudaSuccess)
       mi = b < mi ? b : mi;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, lb_fn((App)a), kBlock, 0) == cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, lb_fn((App)a, B), (int)B, 0) == cudaSuccess)
       ml = b < ml ? b : ml;
   }
   cudaGetLastError();
@@ -127,12 +127,12 @@ TravCtx make_ctx(alb_graph g, bool use_graph, cudaGraphConditionalHandle hw,
 }
 
 static alb_status add_kernel(cudaGraphNode_t* node, cudaGraph_t graph, const cudaGraphNode_t* dep,
-                             size_t ndep, void* fn, uint32_t grid, TravCtx* c) {
+                             size_t ndep, void* fn, uint32_t grid, TravCtx* c, uint32_t block = kBlock) {
   cudaKernelNodeParams kp{};
   void* kargs[] = {c};
   kp.func = fn;
   kp.gridDim = dim3(grid);
-  kp.blockDim = dim3(kBlock);
+  kp.blockDim = dim3(block);
   kp.sharedMemBytes = 0;
   kp.kernelParams = kargs;
   ALB_CUDA_TRY(cudaGraphAddKernelNode(node, graph, dep, ndep, &kp));
@@ -197,7 +197,7 @@ static alb_status build_graph(alb_graph g, App app) {
   wp.conditional.size = 1;
   if (cudaGraphAddNode(&n_while, G, &n_init, nullptr, 1, &wp) != cudaSuccess) return fail(ALB_ERR_CUDA);
   cudaGraph_t body = wp.conditional.phGraph_out[0];
-  if ((rc = add_kernel(&n_insp, body, nullptr, 0, inspect_fn(app), g->blocks, &c)) != ALB_OK)
+  if ((rc = add_kernel(&n_insp, body, nullptr, 0, inspect_fn(app, g->block), g->blocks, &c, g->block)) != ALB_OK)
     return fail(rc);
   cudaGraphNodeParams ip{};
   ip.type = cudaGraphNodeTypeConditional;
@@ -206,7 +206,7 @@ static alb_status build_graph(alb_graph g, App app) {
   ip.conditional.size = 1;
   if (cudaGraphAddNode(&n_if, body, &n_insp, nullptr, 1, &ip) != cudaSuccess) return fail(ALB_ERR_CUDA);
   cudaGraph_t ifbody = ip.conditional.phGraph_out[0];
-  if ((rc = add_kernel(&n_lb, ifbody, nullptr, 0, lb_fn(app), g->lb_blocks, &c)) != ALB_OK)
+  if ((rc = add_kernel(&n_lb, ifbody, nullptr, 0, lb_fn(app, g->block), g->lb_blocks, &c, g->block)) != ALB_OK)
     return fail(rc);
   if (persist_labels(g)) {
     cudaKernelNodeAttrValue v{};
@@ -283,7 +283,7 @@ static alb_status host_loop(alb_graph g, App app, cudaStream_t s) {
     {
       Timer t(prof, s);
       void* args[] = {&c};
-      ALB_CUDA_TRY(cudaLaunchKernel(inspect_fn(app), dim3(g->blocks), dim3(kBlock), args, 0, s));
+      ALB_CUDA_TRY(cudaLaunchKernel(inspect_fn(app, g->block), dim3(g->blocks), dim3(g->block), args, 0, s));
       g->stats.ms_inspect += t.stop();
       g->stats.n_inspect += 1;
     }
@@ -292,7 +292,7 @@ static alb_status host_loop(alb_graph g, App app, cudaStream_t s) {
     if (g->h_st->hub_packed >> 32) {
       Timer t(prof, s);
       void* args[] = {&c};
-      ALB_CUDA_TRY(cudaLaunchKernel(lb_fn(app), dim3(g->lb_blocks), dim3(kBlock), args, 0, s));
+      ALB_CUDA_TRY(cudaLaunchKernel(lb_fn(app, g->block), dim3(g->lb_blocks), dim3(g->block), args, 0, s));
       g->stats.ms_lb += t.stop();
       g->stats.n_lb += 1;
       ALB_CUDA_TRY(cudaMemcpyAsync(g->h_st, g->st, sizeof(RoundState), cudaMemcpyDeviceToHost, s));
@@ -383,7 +383,9 @@ alb_status launch_lb_trace(alb_graph g, const uint32_t* d_work, const uint32_t* 
   k_set_args<<<1, 1, 0, s>>>(g->args, ca);
   TravCtx c = make_ctx(g, false, 0, 0);
   void* args[] = {&c};
-  ALB_CUDA_TRY(cudaLaunchKernel(lb_fn(APP_TRACE), dim3(g->lb_blocks), dim3(kBlock), args, 0, s));
+  // the trace kernel is built for the default CTA size; its grid keeps the handle's thread count
+  const uint32_t trace_grid = (uint32_t)(((uint64_t)g->lb_blocks * g->block + kBlock - 1) / kBlock);
+  ALB_CUDA_TRY(cudaLaunchKernel(lb_fn(APP_TRACE, kBlock), dim3(trace_grid), dim3(kBlock), args, 0, s));
   ALB_CUDA_TRY(cudaGetLastError());
   g->last_stream = s;
   g->last_kind = 0;
@@ -490,7 +492,7 @@ extern "C" alb_status alb_bfs_noalloc(uint32_t n, uint64_t m, const uint32_t* d_
   ALB_CUDA_TRY(cudaGetDevice(&dev));
   ALB_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   uint32_t occ_i = 1, occ_l = 1;
-  occupancy(&occ_i, &occ_l);
+  occupancy(kBlock, &occ_i, &occ_l);
   const uint32_t blocks = (uint32_t)sms * occ_i, lb_blocks = (uint32_t)sms * occ_l;
 
   // validate the caller's CSR (this call's contents of the shared scratch start here)
@@ -533,11 +535,11 @@ extern "C" alb_status alb_bfs_noalloc(uint32_t n, uint64_t m, const uint32_t* d_
   ALB_CUDA_TRY(cudaLaunchKernel((void*)k_init<APP_BFS>, dim3(blocks), dim3(kBlock), kargs, 0, s));
   RoundState hs{};
   for (;;) {
-    ALB_CUDA_TRY(cudaLaunchKernel((void*)k_inspect<BfsOp>, dim3(blocks), dim3(kBlock), kargs, 0, s));
+    ALB_CUDA_TRY(cudaLaunchKernel((void*)k_inspect<BfsOp, kBlock>, dim3(blocks), dim3(kBlock), kargs, 0, s));
     ALB_CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s));
     ALB_CUDA_TRY(cudaStreamSynchronize(s));
     if (hs.hub_packed >> 32) {
-      ALB_CUDA_TRY(cudaLaunchKernel((void*)k_lb<BfsOp, false>, dim3(lb_blocks), dim3(kBlock), kargs, 0, s));
+      ALB_CUDA_TRY(cudaLaunchKernel((void*)k_lb<BfsOp, false, kBlock>, dim3(lb_blocks), dim3(kBlock), kargs, 0, s));
       ALB_CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s));
       ALB_CUDA_TRY(cudaStreamSynchronize(s));
     }

@@ -2,7 +2,8 @@
 // paper finds a wide flat range, Sec. 5.1 "Analyzing Threshold") and the TWC bin cut-offs.
 // Coordinate search timed on the device: first the threshold over powers of 4 plus the paper's
 // rule (threads of the LB kernel) and "never huge", then the CTA and warp cut-offs at the best
-// threshold. The fastest setting is left applied to that application on the handle.
+// threshold, then the round kernels' CTA size (128, 256, 512; Sec. 5.1 uses 2^8 threads). The
+// fastest setting is left applied to that application on the handle.
 #include <cfloat>
 #include <vector>
 
@@ -107,6 +108,18 @@ extern "C" alb_status alb_autotune(alb_graph g, alb_app app, uint32_t src, uint3
         if ((rc = trial(cur)) != ALB_OK) break;
       }
       if (rc != ALB_OK) break;
+    }
+  }
+  // 3) CTA size of the round kernels at the best threshold and cut-offs (PageRank's kernels have
+  //    a fixed CTA size)
+  if (rc == ALB_OK && app != ALB_APP_PAGERANK) {
+    const alb_params at = top;
+    const uint32_t at_b = at.block_size ? at.block_size : (uint32_t)kBlock;
+    for (uint32_t b : {128u, 256u, 512u}) {
+      if (b == at_b) continue;
+      cur = at;
+      cur.block_size = b;
+      if ((rc = trial(cur)) != ALB_OK) break;
     }
   }
   cudaFree(out);

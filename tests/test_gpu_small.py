@@ -60,6 +60,8 @@ def oracle_all(g, src, k=3):
 
 SETTINGS = [
     dict(hub_threshold=-1),
+    dict(hub_threshold=3, twc_warp_min=1, twc_cta_min=2, block_size=128),
+    dict(hub_threshold=5, twc_warp_min=2, twc_cta_min=3, block_size=512, distribution=1),
     dict(hub_threshold=0),
     dict(hub_threshold=1),
     dict(hub_threshold=3, twc_warp_min=1, twc_cta_min=2),
@@ -106,6 +108,43 @@ def test_threshold_sweep_identical_results(rmat13, t):
     # the source is the max-degree vertex: it is huge whenever t <= max degree
     assert (st["hub_rounds"] > 0) == (0 <= t <= int(g.degrees().max()))
     assert st["edges_twc"] + st["edges_lb"] == int(g.degrees()[host(o) != 0xFFFFFFFF].sum())
+    G.close()
+
+
+@pytest.mark.parametrize("block_size", [128, 256, 512])
+@pytest.mark.parametrize("t", [-1, 0, 64, 3000])
+def test_cta_sizes_identical_results(rmat13, block_size, t):
+    """The round kernels built for 128, 256 and 512 threads per CTA give the oracle's results at
+    every threshold; the paper's rule follows the LB kernel's thread count."""
+    g = rmat13
+    src = g.max_degree_vertex()
+    G = make(g)
+    G.set_params(hub_threshold=t, block_size=block_size)
+    got = run_all(G, g, src, k=16)
+    ref = oracle_all(g, src, k=16)
+    for app in ref:
+        assert np.array_equal(got[app], ref[app]), app
+    o = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    G.bfs(src, o)
+    st = G.stats()
+    assert st["block_size"] == block_size and st["lb_threads"] % block_size == 0
+    if t == -1:
+        assert st["hub_threshold"] == st["lb_threads"]
+    srcs = np.array([0, 7, 100, 4095, src], dtype=np.uint32)   # the batched path takes it too
+    out = torch.empty(len(srcs) * g.n, dtype=torch.int32, device="cuda")
+    G.sssp_batch(srcs, out)
+    res = host(out).reshape(len(srcs), g.n)
+    for i, s in enumerate(srcs):
+        assert np.array_equal(res[i], oracle.sssp(g.n, g.offsets, g.indices, g.weights, int(s))), i
+    G.close()
+
+
+def test_cta_size_argument_errors(rmat13):
+    G = make(rmat13)
+    for bad in (64, 100, 1024):
+        with pytest.raises(alb.AlbError) as e:
+            G.set_params(block_size=bad)
+        assert e.value.code == 1
     G.close()
 
 
@@ -393,8 +432,10 @@ def test_autotune_keeps_results_exact(rmat13, app):
     assert ms > 0
     assert p.hub_threshold in [-1, 1 << 40] + [1 << k for k in range(8, 21, 2)]
     assert p.twc_cta_min in (128, 256, 512, 1024) and p.twc_warp_min in (16, 32, 64)
+    assert p.block_size in (128, 256, 512)
     q = G.params(app)
-    assert (q.hub_threshold, q.twc_cta_min, q.twc_warp_min) == (p.hub_threshold, p.twc_cta_min, p.twc_warp_min)
+    assert (q.hub_threshold, q.twc_cta_min, q.twc_warp_min, q.block_size) == \
+        (p.hub_threshold, p.twc_cta_min, p.twc_warp_min, p.block_size)
     got = run_all(G, g, src, k=32)
     ref = oracle_all(g, src, k=32)
     for a in ref:
