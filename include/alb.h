@@ -289,7 +289,7 @@ uint32_t alb_threshold_rule(uint32_t num_sms, uint32_t threads_per_sm);
  * the device in cudaMalloc/cudaFree. The paper has no counterpart: this is a
  * packaging of the same bfs path (same kernels and results as alb_bfs with
  * default parameters). It needs no alb_graph and never allocates: its scratch
- * (frontiers, huge worklist and prefix sums, round state; about 16.8 MB) is one
+ * (frontiers, huge worklist and prefix sums, visited bitmap, round state; about 16.9 MB) is one
  * fixed array in the library's device image, held on every GPU that loads the
  * library until the process exits.
  *   n <= ALB_NOALLOC_MAX_VERTICES, else ALB_ERR_INVALID_ARG (nothing enqueued);

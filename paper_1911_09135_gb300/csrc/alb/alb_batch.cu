@@ -200,11 +200,14 @@ __global__ void __launch_bounds__(kBlock) k_multi_init(TravCtx c) {
   uint32_t* lab = c.args->lab;
   for (uint64_t v = (uint64_t)blockIdx.x * kBlock + threadIdx.x; v < c.n; v += (uint64_t)gridDim.x * kBlock)
     lab[v] = kInf;
-  if (APP == APP_SSSP && c.pushed)
-    for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < 2ull * c.pw; i += (uint64_t)gridDim.x * kBlock)
+  // sssp: both push bitmaps start empty; bfs: the visited bitmap (the seed kernel sets the sources)
+  const uint64_t words = APP == APP_SSSP ? 2ull * c.pw : (uint64_t)c.pw;
+  if (c.pushed)
+    for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < words; i += (uint64_t)gridDim.x * kBlock)
       c.pushed[i] = 0u;
 }
 
+template <int APP>
 __global__ void k_multi_seed(TravCtx c) {
   const CallArgs* ca = c.args;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ca->nsrc; i += gridDim.x * blockDim.x) {
@@ -214,6 +217,7 @@ __global__ void k_multi_seed(TravCtx c) {
       continue;
     }
     if (atomicCAS(ca->lab + v, kInf, 0u) == kInf) {
+      if (APP == APP_BFS) atomicOr(c.pushed + (v >> 5), 1u << (v & 31u));  // visited
       const uint32_t slot = atomicAdd(&c.st->fcount[0], 1u);
       if (ALB_IN_RANGE(c.chk, CHK_PUSH, slot, c.n)) c.F0[slot] = v;
     }
@@ -359,12 +363,12 @@ static BatchCfg batch_cfg(alb_graph g, BatchKind kind) {
       k.insp = inspect_for<MsSsspOp>(g->block); k.lb = lb_for<MsSsspOp>(g->block);
       break;
     case BK_MULTI_BFS:
-      k.init = (void*)k_multi_init<APP_BFS>; k.seed = (void*)k_multi_seed;
+      k.init = (void*)k_multi_init<APP_BFS>; k.seed = (void*)k_multi_seed<APP_BFS>;
       k.insp = inspect_for<BfsOp>(g->block); k.lb = lb_for<BfsOp>(g->block);
       k.seed_grid = g->blocks; k.seed_block = kBlock;
       break;
     default:
-      k.init = (void*)k_multi_init<APP_SSSP>; k.seed = (void*)k_multi_seed;
+      k.init = (void*)k_multi_init<APP_SSSP>; k.seed = (void*)k_multi_seed<APP_SSSP>;
       k.insp = inspect_for<SsspOp>(g->block); k.lb = lb_for<SsspOp>(g->block);
       k.seed_grid = g->blocks; k.seed_block = kBlock;
       break;

@@ -27,7 +27,7 @@ namespace alb {
 
 struct OpArgs {
   uint32_t* lab;
-  uint32_t* pushed;  // this round's push bitmap (sssp, cc)
+  uint32_t* pushed;  // this round's push bitmap (sssp, cc); the visited bitmap (bfs)
   uint32_t next;     // round + 1
   uint32_t k;
   const void* aux;  // operator-specific state (the multi-source operators)
@@ -35,10 +35,15 @@ struct OpArgs {
   uint32_t* chk;    // checked build
 };
 
-// bfs (push): level[dst] = round + 1 if unvisited.
+// bfs (push): level[dst] = round + 1 if unvisited. Visited vertices are kept in a bitmap (one bit
+// per vertex, set once for the whole traversal): the per-edge probe reads a bitmap word, which
+// stays in L2 (2 MB at 2^24 vertices) where the 4-byte level array (64 MB) would compete with the
+// streamed CSR, and the atomicOr that sets the bit claims the vertex, whose level is then a plain
+// store.
 struct BfsOp {
   static constexpr bool kBatch = false;
   static constexpr bool kW = false;
+  static constexpr bool kVisited = true;
   __device__ static uint32_t sval(const OpArgs&, uint32_t) { return 0u; }
   __device__ static bool want(const OpArgs&, uint32_t, uint32_t cur, uint32_t) { return cur == kInf; }
   __device__ static bool commit(const OpArgs& a, uint32_t, uint32_t dst, uint32_t) {
@@ -147,6 +152,19 @@ struct KcoreOp {
   }
   __device__ static bool commit(const OpArgs& a, uint32_t, uint32_t dst, uint32_t) { return commit_n(a, dst, 1u); }
 };
+
+template <class Op, class = void>
+struct uses_visited { static constexpr bool value = false; };
+template <class Op>
+struct uses_visited<Op, decltype(void(Op::kVisited))> { static constexpr bool value = Op::kVisited; };
+
+// The bitmap an operator's OpArgs carries in round parity `cur`: the round's push bitmap, or the
+// traversal-wide visited bitmap (bitmap 0).
+template <class Op>
+__device__ __forceinline__ uint32_t* op_bitmap(const TravCtx& c, uint32_t cur) {
+  if (!c.pushed) return nullptr;
+  return uses_visited<Op>::value ? c.pushed : c.pushed + (size_t)cur * c.pw;
+}
 
 template <class Op, class = void>
 struct uses_push_bitmap { static constexpr bool value = false; };
@@ -302,6 +320,24 @@ __device__ __forceinline__ void relax(const TravCtx& c, const OpArgs& a, const u
       }
     }
     push_n<U>(push, dst, sink);
+  } else if constexpr (uses_visited<Op>::value) {
+    // probe the visited bitmap; the atomicOr that sets a bit claims the vertex (U of each issued
+    // before any result is used), and the claimant stores the level
+    uint32_t wd[U], old[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) wd[u] = ok[u] ? a.pushed[dst[u] >> 5] : 0xFFFFFFFFu;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t bit = 1u << (dst[u] & 31u);
+      old[u] = (wd[u] & bit) ? bit : atomicOr(a.pushed + (dst[u] >> 5), bit);
+    }
+    bool push[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) push[u] = ok[u] && !(old[u] & (1u << (dst[u] & 31u)));
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (push[u]) a.lab[dst[u]] = a.next;
+    push_n<U>(push, dst, sink);
   } else {
     uint32_t cur[U];
 #pragma unroll
@@ -423,7 +459,7 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_inspe
   uint32_t* Fn = cur ? c.F0 : c.F1;
   uint32_t* ncount = &st->fcount[cur ^ 1u];
   const CallArgs* ca = c.args;
-  const OpArgs a{ca->lab, c.pushed ? c.pushed + (size_t)cur * c.pw : nullptr, r + 1u, ca->k, ca->aux, c.n, c.chk};
+  const OpArgs a{ca->lab, op_bitmap<Op>(c, cur), r + 1u, ca->k, ca->aux, c.n, c.chk};
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   unsigned long long twc_edges = 0ull;
   const PushSink sink{Fn, ncount, c.n, c.chk, s_push, &s_npush, kPushBufOf<B>};
@@ -590,7 +626,7 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_lb(Tr
   uint32_t* Fn = cur ? c.F0 : c.F1;
   uint32_t* ncount = &st->fcount[cur ^ 1u];
   const CallArgs* ca = c.args;
-  const OpArgs a{ca->lab, c.pushed ? c.pushed + (size_t)cur * c.pw : nullptr, r + 1u, ca->k, ca->aux, c.n, c.chk};
+  const OpArgs a{ca->lab, op_bitmap<Op>(c, cur), r + 1u, ca->k, ca->aux, c.n, c.chk};
   const uint32_t tid = threadIdx.x, lane = tid & 31u;
   // a step of the CTA is B x U positions, at most one push each: the buffer never overflows
   static_assert(kTrace || B * (Op::kBatch ? kUMs : kULb) <= kPushBufOf<B>,
@@ -735,6 +771,10 @@ __global__ void __launch_bounds__(kBlock) k_init(TravCtx c) {
   if constexpr (APP == APP_SSSP || APP == APP_CC) {  // both push bitmaps start empty
     for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < 2ull * c.pw; i += (uint64_t)gridDim.x * kBlock)
       c.pushed[i] = 0u;
+  }
+  if constexpr (APP == APP_BFS) {  // the visited bitmap starts with the source alone
+    for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < c.pw; i += (uint64_t)gridDim.x * kBlock)
+      c.pushed[i] = (i == (src >> 5)) ? 1u << (src & 31u) : 0u;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if constexpr (APP == APP_BFS || APP == APP_SSSP) { c.F0[0] = src; st->fcount[0] = 1u; }

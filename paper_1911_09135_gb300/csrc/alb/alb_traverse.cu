@@ -411,7 +411,8 @@ namespace alb {
 
 constexpr uint32_t kNoAllocMaxVertices = 1u << 20;
 constexpr size_t kNoAllocVec = ((sizeof(uint32_t) * ((size_t)kNoAllocMaxVertices + 1) + 255) / 256) * 256;
-constexpr size_t kNoAllocBytes = 4 * kNoAllocVec + 4 * 256;
+constexpr size_t kNoAllocBits = ((sizeof(uint32_t) * ((size_t)kNoAllocMaxVertices / 32 + 1) + 255) / 256) * 256;
+constexpr size_t kNoAllocBytes = 4 * kNoAllocVec + kNoAllocBits + 4 * 256;
 
 // Shared by every call on a device: calls whose work overlaps on the GPU race on it.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -482,10 +483,12 @@ extern "C" alb_status alb_bfs_noalloc(uint32_t n, uint64_t m, const uint32_t* d_
   uint32_t* F1 = reinterpret_cast<uint32_t*>(base + kNoAllocVec);
   uint32_t* hub_v = reinterpret_cast<uint32_t*>(base + 2 * kNoAllocVec);
   uint32_t* hub_p = reinterpret_cast<uint32_t*>(base + 3 * kNoAllocVec);
-  RoundState* st = reinterpret_cast<RoundState*>(base + 4 * kNoAllocVec);
-  CallArgs* args = reinterpret_cast<CallArgs*>(base + 4 * kNoAllocVec + 256);
-  NoAllocCheck* chk = reinterpret_cast<NoAllocCheck*>(base + 4 * kNoAllocVec + 512);
-  uint32_t* bounds = reinterpret_cast<uint32_t*>(base + 4 * kNoAllocVec + 768);  // TravCtx::chk
+  uint32_t* visited = reinterpret_cast<uint32_t*>(base + 4 * kNoAllocVec);  // bfs visited bitmap
+  unsigned char* small = base + 4 * kNoAllocVec + kNoAllocBits;
+  RoundState* st = reinterpret_cast<RoundState*>(small);
+  CallArgs* args = reinterpret_cast<CallArgs*>(small + 256);
+  NoAllocCheck* chk = reinterpret_cast<NoAllocCheck*>(small + 512);
+  uint32_t* bounds = reinterpret_cast<uint32_t*>(small + 768);  // TravCtx::chk
   static_assert(sizeof(RoundState) <= 256 && sizeof(CallArgs) <= 256, "scratch layout");
 
   int dev = 0, sms = 0;
@@ -520,8 +523,8 @@ extern "C" alb_status alb_bfs_noalloc(uint32_t n, uint64_t m, const uint32_t* d_
   c.F1 = F1;
   c.hub_v = hub_v;
   c.hub_p = hub_p;
-  c.pushed = nullptr;  // bfs needs no push bitmaps
-  c.pw = 0u;
+  c.pushed = visited;  // cleared by the init kernel
+  c.pw = (n + 31u) / 32u;
   c.st = st;
   c.args = args;
   c.m = (uint32_t)m;   // bound of the edge indices in the bounds-checked build
