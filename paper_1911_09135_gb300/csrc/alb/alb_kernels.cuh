@@ -210,7 +210,9 @@ __device__ __forceinline__ bool hot_add(uint32_t* key, uint32_t* cnt, uint32_t v
 // atomics serialise in L2, so the TWC kernel collects a tile's pushes in shared memory (one
 // shared atomic per warp and step) and moves them to the frontier with one global atomic per
 // tile. Pushes that do not fit in the buffer go to the frontier directly.
-// Staging entries per CTA: 2048, or one LB step of the CTA (B threads x 8 positions) if larger.
+// Staging entries per CTA: the inspection kernel's tile buffer, and the LB kernel's: 2048, or one
+// LB step of the CTA (B threads x 8 positions) if larger.
+constexpr uint32_t kTilePushBuf = 2048;
 template <int B>
 constexpr uint32_t kPushBufOf = (uint32_t)B * 8u > 2048u ? (uint32_t)B * 8u : 2048u;
 
@@ -414,6 +416,12 @@ static __device__ __forceinline__ void hub_append(bool huge, uint32_t v, uint32_
 // latency chain: +8 % over bfs, sssp, cc and k-core on rmat24-hubs); 4 for the multi-source
 // operators, which hold a row of labels per edge (5 spilled up to 272 bytes; with no minimum,
 // ptxas gave them up to 118 registers and 2 CTAs per SM, 1.4x slower batches).
+// Entries of the inspection kernel's thread-bin owner map: 16 edge positions per thread (12 for
+// k-core at 512 threads, whose CTA table shares the 48 KB of static shared memory); positions
+// beyond it are found by binary search of the bin's scan.
+template <class Op, int B>
+constexpr uint32_t kOwnerMapOf = (aggregates<Op>::value && B >= 512) ? 12u * B : 16u * B;
+
 template <class Op, int B>
 constexpr int round_kernel_min_blocks() { return (Op::kBatch ? 4 : 5) * kBlock / B; }
 
@@ -438,7 +446,9 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_inspe
   constexpr int UC = Op::kBatch ? kUMs : kUCta;  // edges in flight per thread, per bin
   constexpr int UW = Op::kBatch ? kUMs : kUWarp;
   constexpr int UT = Op::kBatch ? (kUMs < kUThread ? kUMs : kUThread) : kUThread;
-  __shared__ uint32_t s_push[kPushBufOf<B>];  // the tile's pushes (PushSink)
+  __shared__ uint32_t s_push[kTilePushBuf];  // the tile's pushes (PushSink)
+  constexpr uint32_t kMap = kOwnerMapOf<Op, B>;
+  __shared__ uint16_t s_own[kMap];  // thread-bin edge position -> the thread (vertex) owning it
   __shared__ uint32_t s_npush, s_pbase;
   constexpr bool kHot = aggregates<Op>::value;
   constexpr uint32_t kHotN = kHot ? kHotSlots : 1u;
@@ -462,7 +472,7 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_inspe
   const OpArgs a{ca->lab, op_bitmap<Op>(c, cur), r + 1u, ca->k, ca->aux, c.n, c.chk};
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   unsigned long long twc_edges = 0ull;
-  const PushSink sink{Fn, ncount, c.n, c.chk, s_push, &s_npush, kPushBufOf<B>};
+  const PushSink sink{Fn, ncount, c.n, c.chk, s_push, &s_npush, kTilePushBuf};
   if constexpr (uses_push_bitmap<Op>::value) {
     // the other bitmap (last round's) is cleared for the next round
     if (c.pushed) {
@@ -517,6 +527,11 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_inspe
     s_sb[tid] = beg;
     s_sv[tid] = sv;
     if (tid == 0) s_scan[B] = stotal;
+    {
+      // the thread bin's owner map: each small vertex marks its run of positions (the first kMap)
+      const uint32_t end = ex + sdeg < kMap ? ex + sdeg : kMap;
+      for (uint32_t q = ex; q < end; ++q) s_own[q] = (uint16_t)tid;
+    }
     __syncthreads();
 
     // CTA bin: the whole CTA expands one vertex at a time.
@@ -562,7 +577,7 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_inspe
         ok[u] = q < S;
         e[u] = 0u; s2[u] = 0u;
         if (ok[u]) {
-          owner = upper_search(s_scan, owner, B, q);
+          owner = q < kMap ? (uint32_t)s_own[q] : upper_search(s_scan, owner, B, q);
           e[u] = s_sb[owner] + (q - s_scan[owner]);
           s2[u] = s_sv[owner];
         }
@@ -649,10 +664,10 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_lb(Tr
   __syncthreads();
   const uint32_t* P = staged ? s_p : c.hub_p;
 
-  // source lookup for position k; j only grows along a thread's positions
+  // source lookup for position k, starting from j0 (P[j0] <= k); a thread's positions only grow
   uint32_t j = 0u, jc = kInf, base_c = 0u, val_c = 0u, src_c = 0u;
-  auto resolve = [&](uint32_t k, uint32_t& edge, uint32_t& sv, uint32_t& src) {
-    j = advance_search(P, j, nh, k);
+  auto resolve = [&](uint32_t k, uint32_t j0, uint32_t& edge, uint32_t& sv, uint32_t& src) {
+    j = advance_search(P, j0 > j ? j0 : j, nh, k);
     if (!ALB_IN_RANGE(c.chk, CHK_SRC, j, nh)) j = 0u;
     if (staged) {
       edge = k + s_base[j];
@@ -675,13 +690,18 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_lb(Tr
   const uint64_t gt = (uint64_t)blockIdx.x * B + tid;
   constexpr int U = Op::kBatch ? kUMs : kULb;
   unsigned long long lb_edges = 0ull;  // positions this thread processed (cta_stats)
-  auto process = [&](const uint64_t (&k)[U], const bool (&ok)[U]) {
+  // kw: the warp's first position of each slot in the cyclic distribution (warp-uniform; its
+  // search gives every lane of the warp a huge vertex at or before its own position to start
+  // from), null in the blocked one
+  uint32_t jw = 0u;
+  auto process = [&](const uint64_t (&k)[U], const bool (&ok)[U], const uint64_t* kw) {
     uint32_t ed[U], sv[U], src[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       ed[u] = 0u; sv[u] = 0u; src[u] = 0u;
+      if (kw && kw[u] < e) jw = upper_search(P, jw, nh, (uint32_t)kw[u]);
       if (ok[u]) {
-        resolve((uint32_t)k[u], ed[u], sv[u], src[u]);
+        resolve((uint32_t)k[u], kw ? jw : 0u, ed[u], sv[u], src[u]);
         ++lb_edges;
       }
     }
@@ -709,15 +729,23 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_lb(Tr
     }
   };
   if (c.distribution == 0u) {
-    // cyclic: thread gt takes positions gt, gt + p, gt + 2p, ... (Sec. 4.1)
+    // cyclic: thread gt takes positions gt, gt + p, gt + 2p, ... (Sec. 4.1). The 32 lanes of a
+    // warp hold 32 consecutive positions, which nearly always fall in one huge vertex's edges, so
+    // the warp searches prefixWork once for its first position (uniform, broadcast reads) and
+    // each lane only steps forward from there; a thread's own successive positions are p apart
+    // and would each need a full search.
     const uint64_t cta0 = (uint64_t)blockIdx.x * B;
     for (uint64_t c0 = cta0; c0 < e; c0 += p * U) {  // CTA-uniform
-      const uint64_t k0 = c0 + (gt - cta0) - lane;
-      uint64_t k[U];
+      const uint64_t k0 = c0 + (gt - cta0) - lane;  // the warp's first position
+      uint64_t k[U], kw[U];
       bool ok[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) { k[u] = k0 + lane + (uint64_t)u * p; ok[u] = k[u] < e; }
-      process(k, ok);
+      for (int u = 0; u < U; ++u) {
+        kw[u] = k0 + (uint64_t)u * p;
+        k[u] = kw[u] + lane;
+        ok[u] = k[u] < e;
+      }
+      process(k, ok, kw);
       flush();
     }
   } else {
@@ -730,7 +758,7 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_lb(Tr
       bool ok[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) { k[u] = lo + i0 + u; ok[u] = k[u] < hi; }
-      process(k, ok);
+      process(k, ok, nullptr);
       flush();
     }
   }
