@@ -664,10 +664,10 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_lb(Tr
   __syncthreads();
   const uint32_t* P = staged ? s_p : c.hub_p;
 
-  // source lookup for position k, starting from j0 (P[j0] <= k); a thread's positions only grow
+  // source lookup for position k; j only grows along a thread's positions
   uint32_t j = 0u, jc = kInf, base_c = 0u, val_c = 0u, src_c = 0u;
-  auto resolve = [&](uint32_t k, uint32_t j0, uint32_t& edge, uint32_t& sv, uint32_t& src) {
-    j = advance_search(P, j0 > j ? j0 : j, nh, k);
+  auto resolve = [&](uint32_t k, uint32_t& edge, uint32_t& sv, uint32_t& src) {
+    j = advance_search(P, j, nh, k);
     if (!ALB_IN_RANGE(c.chk, CHK_SRC, j, nh)) j = 0u;
     if (staged) {
       edge = k + s_base[j];
@@ -690,18 +690,13 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_lb(Tr
   const uint64_t gt = (uint64_t)blockIdx.x * B + tid;
   constexpr int U = Op::kBatch ? kUMs : kULb;
   unsigned long long lb_edges = 0ull;  // positions this thread processed (cta_stats)
-  // kw: the warp's first position of each slot in the cyclic distribution (warp-uniform; its
-  // search gives every lane of the warp a huge vertex at or before its own position to start
-  // from), null in the blocked one
-  uint32_t jw = 0u;
-  auto process = [&](const uint64_t (&k)[U], const bool (&ok)[U], const uint64_t* kw) {
+  auto process = [&](const uint64_t (&k)[U], const bool (&ok)[U]) {
     uint32_t ed[U], sv[U], src[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       ed[u] = 0u; sv[u] = 0u; src[u] = 0u;
-      if (kw && kw[u] < e) jw = upper_search(P, jw, nh, (uint32_t)kw[u]);
       if (ok[u]) {
-        resolve((uint32_t)k[u], kw ? jw : 0u, ed[u], sv[u], src[u]);
+        resolve((uint32_t)k[u], ed[u], sv[u], src[u]);
         ++lb_edges;
       }
     }
@@ -729,23 +724,15 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_lb(Tr
     }
   };
   if (c.distribution == 0u) {
-    // cyclic: thread gt takes positions gt, gt + p, gt + 2p, ... (Sec. 4.1). The 32 lanes of a
-    // warp hold 32 consecutive positions, which nearly always fall in one huge vertex's edges, so
-    // the warp searches prefixWork once for its first position (uniform, broadcast reads) and
-    // each lane only steps forward from there; a thread's own successive positions are p apart
-    // and would each need a full search.
+    // cyclic: thread gt takes positions gt, gt + p, gt + 2p, ... (Sec. 4.1)
     const uint64_t cta0 = (uint64_t)blockIdx.x * B;
     for (uint64_t c0 = cta0; c0 < e; c0 += p * U) {  // CTA-uniform
-      const uint64_t k0 = c0 + (gt - cta0) - lane;  // the warp's first position
-      uint64_t k[U], kw[U];
+      const uint64_t k0 = c0 + (gt - cta0) - lane;
+      uint64_t k[U];
       bool ok[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        kw[u] = k0 + (uint64_t)u * p;
-        k[u] = kw[u] + lane;
-        ok[u] = k[u] < e;
-      }
-      process(k, ok, kw);
+      for (int u = 0; u < U; ++u) { k[u] = k0 + lane + (uint64_t)u * p; ok[u] = k[u] < e; }
+      process(k, ok);
       flush();
     }
   } else {
@@ -758,7 +745,7 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_lb(Tr
       bool ok[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) { k[u] = lo + i0 + u; ok[u] = k[u] < hi; }
-      process(k, ok, nullptr);
+      process(k, ok);
       flush();
     }
   }
