@@ -664,10 +664,10 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_lb(Tr
   __syncthreads();
   const uint32_t* P = staged ? s_p : c.hub_p;
 
-  // source lookup for position k; j only grows along a thread's positions
+  // source lookup for position k, from j0 (P[j0] <= k); a thread's positions only grow
   uint32_t j = 0u, jc = kInf, base_c = 0u, val_c = 0u, src_c = 0u;
-  auto resolve = [&](uint32_t k, uint32_t& edge, uint32_t& sv, uint32_t& src) {
-    j = advance_search(P, j, nh, k);
+  auto resolve = [&](uint32_t k, uint32_t j0, uint32_t& edge, uint32_t& sv, uint32_t& src) {
+    j = advance_search(P, j0 > j ? j0 : j, nh, k);
     if (!ALB_IN_RANGE(c.chk, CHK_SRC, j, nh)) j = 0u;
     if (staged) {
       edge = k + s_base[j];
@@ -690,13 +690,29 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_lb(Tr
   const uint64_t gt = (uint64_t)blockIdx.x * B + tid;
   constexpr int U = Op::kBatch ? kUMs : kULb;
   unsigned long long lb_edges = 0ull;  // positions this thread processed (cta_stats)
+  // Cyclic distribution: in every step the CTA's B threads take B consecutive positions per
+  // slot u (c0 + u p + tid), which span one or two huge vertices, while a thread's own positions
+  // are p apart and cross many when the huge vertices average fewer than p edges. Then U lanes
+  // of warp 0 search prefixWork once per step for the CTA's first position of each slot (s_jw[u],
+  // between the step's barriers) and each thread steps forward from there, instead of every
+  // thread binary-searching every position (threshold 4096 on rmat24-hubs: cc 10.4 -> 8.4 ms).
+  // With a few very large huge vertices a thread's own search is one step, and it is kept.
+  __shared__ uint32_t s_jw[U];
+  const bool shared_search = !kTrace && c.distribution == 0u && (uint64_t)e < p * (uint64_t)nh;
+  auto slot_starts = [&](uint64_t c0) {  // warp 0 only; c0 = the CTA's first position of the step
+    if (tid < (uint32_t)U) {
+      const uint64_t kc = c0 + (uint64_t)tid * p;
+      const uint32_t prev = s_jw[tid];
+      s_jw[tid] = kc < e ? upper_search(P, prev, nh, (uint32_t)kc) : prev;
+    }
+  };
   auto process = [&](const uint64_t (&k)[U], const bool (&ok)[U]) {
     uint32_t ed[U], sv[U], src[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       ed[u] = 0u; sv[u] = 0u; src[u] = 0u;
       if (ok[u]) {
-        resolve((uint32_t)k[u], ed[u], sv[u], src[u]);
+        resolve((uint32_t)k[u], shared_search ? s_jw[u] : 0u, ed[u], sv[u], src[u]);
         ++lb_edges;
       }
     }
@@ -714,18 +730,25 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_lb(Tr
     }
   };
 
-  // after each CTA-uniform step: the step's staged pushes go to the frontier in one atomic
-  auto flush = [&]() {
+  // after each CTA-uniform step: the step's staged pushes go to the frontier in one atomic (and,
+  // between the two barriers, the next step's slot starts are found)
+  auto flush = [&](uint64_t next_c0) {
     if constexpr (!kTrace) {
       __syncthreads();
       push_flush(sink, &s_pbase);
       if (threadIdx.x == 0) s_npush = 0u;  // every thread read the count inside push_flush
+      if (shared_search) slot_starts(next_c0);
       __syncthreads();
     }
   };
   if (c.distribution == 0u) {
     // cyclic: thread gt takes positions gt, gt + p, gt + 2p, ... (Sec. 4.1)
     const uint64_t cta0 = (uint64_t)blockIdx.x * B;
+    if (shared_search) {
+      if (tid < (uint32_t)U) s_jw[tid] = 0u;  // P[0] = 0 <= every position
+      slot_starts(cta0);                       // each lane reads and writes its own entry
+      __syncthreads();
+    }
     for (uint64_t c0 = cta0; c0 < e; c0 += p * U) {  // CTA-uniform
       const uint64_t k0 = c0 + (gt - cta0) - lane;
       uint64_t k[U];
@@ -733,7 +756,7 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_lb(Tr
 #pragma unroll
       for (int u = 0; u < U; ++u) { k[u] = k0 + lane + (uint64_t)u * p; ok[u] = k[u] < e; }
       process(k, ok);
-      flush();
+      flush(c0 + p * U);
     }
   } else {
     // blocked: thread gt takes [gt * C, min(e, (gt + 1) * C)), C = ceil(e / p)
@@ -746,7 +769,7 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_lb(Tr
 #pragma unroll
       for (int u = 0; u < U; ++u) { k[u] = lo + i0 + u; ok[u] = k[u] < hi; }
       process(k, ok);
-      flush();
+      flush(0u);
     }
   }
 
