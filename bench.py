@@ -120,6 +120,12 @@ def parse_args():
                          "(ncu cannot profile kernels inside graphs with conditional nodes)")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the paper's default threshold rule instead of the autotuned knobs")
+    ap.add_argument("--hub-threshold", type=int, default=None,
+                    help="a fixed huge-vertex threshold for every app (no autotuning), e.g. for "
+                         "the threshold study or a profiling capture")
+    ap.add_argument("--batch-threshold", type=int, default=None,
+                    help="batch-sources: a fixed threshold for the batched calls instead of the "
+                         "search over candidates")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-roofline", action="store_true")
@@ -400,6 +406,9 @@ def gpu_arm(args, dist):
     if args.apps:
         apps = tuple(a for a in args.apps.split(",") if a in apps)
     step = GpuStep(g, apps, alb, torch)
+    if args.hub_threshold is not None:
+        args.no_tune = True
+        step.G.set_params(hub_threshold=args.hub_threshold)
     # the paper's default rule (threshold = threads of the LB kernel), timed briefly for reference
     paper_rule_ms = None
     if not args.no_tune:
@@ -530,6 +539,7 @@ def gpu_arm(args, dist):
         "run": {"exec_mode": args.exec_mode,
                 "knobs": ("autotuned per app by alb_autotune before timing, on a source other "
                           "than the timed one" if tuned
+                          else f"fixed threshold {args.hub_threshold}" if args.hub_threshold is not None
                           else "paper's rule: threshold = threads of the LB kernel"),
                 "tune_source": int(tsrc) if tuned else None,
                 "tuned": tuned or None,
@@ -760,10 +770,13 @@ def batch_arm(args, dist):
             # chosen by timing a batch of 128 other sources; the TWC cut-offs stay the tuned ones
             cand = sorted({int(tuned.hub_threshold), -1, 1 << 12, 1 << 14, 1 << 16, 1 << 18})
             trial = {}
-            for t in cand:
-                G.set_app_params(app, hub_threshold=t)
-                trial[t] = timed(lambda: batch(G.h, d_tsrcs, 128, out), 1)
-            t_best = min(trial, key=trial.get)
+            if args.batch_threshold is not None:
+                t_best = args.batch_threshold
+            else:
+                for t in cand:
+                    G.set_app_params(app, hub_threshold=t)
+                    trial[t] = timed(lambda: batch(G.h, d_tsrcs, 128, out), 1)
+                t_best = min(trial, key=trial.get)
             G.set_app_params(app, hub_threshold=t_best)
             ms_batch = timed(lambda: batch(G.h, d_srcs, 128, out), args.steps)
             res[app] = {"queries": 128, "ms_plain": round(ms_plain, 3), "ms_batched": round(ms_batch, 3),
