@@ -785,7 +785,20 @@ def batch_arm(args, dist):
                                       "twc_warp_min": tuned.twc_warp_min, "block_size": tuned.block_size},
                         "batched_hub_threshold": t_best,
                         "queries_per_s_batched": round(128 / (ms_batch * 1e-3), 1)}
+        # rounds of the last group of the timed batch (sssp), for the round-overhead estimate below
+        rounds_group = G.stats()["rounds"] if "sssp" in res else None
         G.close()
+        # the per-round floor of the CUDA-graph round loop: bfs along a directed path of 4096
+        # vertices runs 4096 rounds of one vertex each (a persistent multi-round kernel would
+        # replace exactly this cost)
+        P = gg.from_edges(4096, [(i, i + 1) for i in range(4095)], None, symmetrize=False, name="path4096")
+        GP = alb.Graph(P.n, dev(P.offsets), dev(P.indices))
+        po = torch.empty(P.n, dtype=torch.int32, device="cuda")
+        ms_path = timed(lambda: alb.alb_bfs(GP.h, 0, po), 3)
+        GP.close()
+        res["round_floor"] = {"us_per_round": round(1e3 * ms_path / 4096, 2),
+                              "rounds_per_sssp_group": rounds_group,
+                              "note": "bfs on a 4096-vertex directed path / 4096 rounds"}
         desc = (f"128 sources (seed 4) on rmat{args.batch_scale}-sym (scale {args.batch_scale}, ef 16, "
                 f"seed 2, w in [1,100])" + (", host-loop execution" if host_loop else ""))
     else:
@@ -814,6 +827,7 @@ def batch_arm(args, dist):
         desc = (f"512 RMAT graphs, samples log-uniform in [2^10, 2^22] (seed 4), symmetrised, "
                 f"w in [1,100]; union n={u.n} m={u.m}; source 0 of each")
     region.__exit__(None, None, None)
+    floor = res.pop("round_floor", None)
     q = sum(r["queries"] for r in res.values())
     t = sum(r["ms_batched"] for r in res.values())
     tp = sum(r["ms_plain"] for r in res.values())
@@ -823,7 +837,8 @@ def batch_arm(args, dist):
             "step": "one batched call per app (bfs, then sssp) over all the queries",
             "higher_is_better": True, "speedup_vs_plain": round(tp / t, 2),
             "clocks": region.clocks,
-            "config": {"workload": args.workload + ": " + desc}, "per_app": res}
+            "config": {"workload": args.workload + ": " + desc}, "per_app": res,
+            "round_floor": floor}
     if dist.rank == 0:
         print(json.dumps(line), flush=True)
 
