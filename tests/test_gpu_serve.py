@@ -168,3 +168,80 @@ def test_sm_partition_argument_errors():
     finally:
         first.close()
         rest.close()
+
+
+def test_trim_releases_workspaces_and_the_handle_stays_exact():
+    """alb_graph_trim gives back what the handle's calls allocated on first use (batch workspace,
+    cached CUDA graphs, PageRank's vectors) and the next calls set them up again, exactly."""
+    from paper_1911_09135_gb300 import alb
+    g = gg.rmat(16, 16 << 16, 77, symmetrize=True, weighted=True)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
+    G = alb.Graph(g.n, dev(g.offsets), dev(g.indices), dev(g.weights), symmetric=True)
+    try:
+        srcs = np.array([0, 5, g.max_degree_vertex()], dtype=np.uint32)
+        out = torch.empty(3 * g.n, dtype=torch.int32, device="cuda")
+        r = torch.empty(g.n, dtype=torch.float32, device="cuda")
+        for rep in range(2):
+            G.sssp_batch(srcs, out)
+            G.pagerank(0.85, 1e-6, 1000, r)
+            G.sync()
+            got = out.cpu().numpy().view(np.uint32).reshape(3, g.n)
+            for i, s in enumerate(srcs.tolist()):
+                assert np.array_equal(got[i], oracle.sssp(g.n, g.offsets, g.indices, g.weights, s)), (rep, i)
+            if rep == 0:
+                torch.cuda.synchronize()
+                freed = G.trim()
+                # the multi-source workspace alone is 144 bytes per vertex (9.4 MB here); the
+                # device reports free memory in whole pages, so compare with half of it
+                assert freed >= 72 * g.n, freed
+    finally:
+        G.close()
+
+
+def test_eviction_and_reupload_on_the_gpu():
+    """Lazy serving under a memory budget that holds one graph with its buffers: requests for
+    graph 0, then graph 1, then graph 0 again make the server evict idle resources (buffers,
+    cached workspaces through alb_graph_trim, whole graphs) and upload graph 0 again; every result
+    equals the oracle. The free memory the server sees is its own account of what it holds
+    (graphs, slots, buffers, workspaces) under the budget."""
+    gs = [gg.rmat(12, 16 << 12, 610 + i, symmetrize=True, weighted=True) for i in range(2)]
+    full = max(serve.csr_bytes(g) + serve.ROUND_WS_PER_VERTEX * g.n
+               + sum(serve.result_bytes(g.n, k) for k in serve.KINDS) + serve.BATCH_WS_PER_VERTEX * g.n
+               for g in gs)
+    up = max(serve.csr_bytes(g) + serve.ROUND_WS_PER_VERTEX * g.n for g in gs)
+    budget = full + up // 2
+    holder = {}
+
+    def held():
+        srv = holder["srv"]
+        used = 0
+        for gr in srv.graphs:
+            if not gr.resident:
+                continue
+            used += gr.upload_bytes() + gr.clone_bytes() * (len(gr.slots) - 1)
+            for s in gr.slots:
+                used += sum(serve.result_bytes(s.n, k) for k in s.bufs)
+                if s.warmed & {"bfs", "sssp"}:
+                    used += serve.BATCH_WS_PER_VERTEX * s.n
+        return budget - used, budget
+
+    srv = serve.Server(gs, tune=False, keep_results=True, lazy=True, hbm_reserve=0,
+                       mem_get_info=lambda: held())
+    holder["srv"] = srv
+    kinds = serve.KINDS
+    reqs = [serve.Request(i, 0.05 * (i // 30), (i // 30) % 2, kinds[i % 3], 1 + (i * 37) % 4000)
+            for i in range(90)]
+    try:
+        srv.run(reqs, realtime=True, timeout=120)
+    finally:
+        srv.close()
+    assert srv.evictions > 0 and srv.graphs[0].uploads == 2
+    for r in reqs:
+        g = gs[r.graph]
+        if r.kind == "bfs":
+            ref = oracle.bfs(g.n, g.offsets, g.indices, r.src)
+        elif r.kind == "sssp":
+            ref = oracle.sssp(g.n, g.offsets, g.indices, g.weights, r.src)
+        else:
+            ref = oracle.cc(g.n, g.offsets, g.indices)
+        assert np.array_equal(srv.results[r.rid], ref), (r.rid, r.kind, r.graph)
