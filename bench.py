@@ -510,7 +510,8 @@ def gpu_arm(args, dist):
         cores = len(os.sched_getaffinity(0))
         t_or = time.perf_counter()
         x_ref, it_ref, _ = oracle.pagerank(g.n, g.offsets, g.indices, PR_D, PR_TOL, PR_MAX,
-                                           assume_symmetric=g.symmetric, nthreads=cores)
+                                           assume_symmetric=g.symmetric, nthreads=cores,
+                                           cache_key=g.key)
         pr_oracle = {"l1_vs_oracle": float(np.abs(pr_gpu - x_ref).sum()), "oracle_iterations": it_ref,
                      "oracle_s": round(time.perf_counter() - t_or, 1), "oracle_cores": cores}
     cpu = None
@@ -669,7 +670,7 @@ def reference_arm(args, dist):
     if "pr" in apps:
         _, pr_iters, _ = oracle.pagerank(g.n, g.offsets, g.indices, PR_D, PR_TOL, PR_MAX,
                                          assume_symmetric=g.symmetric,
-                                         nthreads=len(os.sched_getaffinity(0)))
+                                         nthreads=len(os.sched_getaffinity(0)), cache_key=g.key)
         step_units["pr"] = int(g.m) * pr_iters
     cheap = min(apps, key=lambda a: {"kcore": 0, "bfs": 1, "cc": 2, "pr": 3, "sssp": 4}[a])
     for _ in range(max(args.warmup, 0)):

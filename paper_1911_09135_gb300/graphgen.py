@@ -18,6 +18,8 @@ from __future__ import annotations
 
 import ctypes
 import dataclasses
+import hashlib
+import json
 import math
 import os
 
@@ -86,6 +88,7 @@ class CSR:
     symmetric: bool = False
     hubs: np.ndarray | None = None   # injected hub ids, if any
     name: str = ""
+    key: str | None = None           # generator graphs: a digest of the recipe and the generator
 
     @property
     def m(self) -> int:
@@ -100,11 +103,57 @@ class CSR:
         return int(np.argmax(d)) if self.n else 0
 
 
+# On-disk cache of generated graphs: set ALB_GRAPH_CACHE to a directory and every rmat() graph is
+# stored there once (numpy .npz) under a digest of its recipe and of the generator's source, and
+# loaded from there afterwards (a scale-24 graph takes far longer to draw than to read).
+CACHE_ENV = "ALB_GRAPH_CACHE"
+
+
+def _recipe_key(**recipe) -> str:
+    src = os.path.join(_build.CSRC, "gen", "graphgen.cpp")
+    h = hashlib.sha256(open(src, "rb").read())
+    h.update(json.dumps(recipe, sort_keys=True).encode())
+    return h.hexdigest()[:32]
+
+
+def _cache_load(key: str, name: str, symmetrize: bool) -> CSR | None:
+    cdir = os.environ.get(CACHE_ENV)
+    path = os.path.join(cdir, key + ".npz") if cdir else None
+    if not path or not os.path.exists(path):
+        return None
+    z = np.load(path)
+    w = z["weights"] if "weights" in z.files else None
+    hubs = z["hubs"] if "hubs" in z.files else None
+    return CSR(n=int(z["offsets"].shape[0]) - 1, offsets=z["offsets"], indices=z["indices"],
+               weights=w, symmetric=symmetrize, hubs=hubs, name=name, key=key)
+
+
+def _cache_store(g: CSR) -> None:
+    cdir = os.environ.get(CACHE_ENV)
+    if not cdir or not g.key:
+        return
+    os.makedirs(cdir, exist_ok=True)
+    arrays = {"offsets": g.offsets, "indices": g.indices}
+    if g.weights is not None:
+        arrays["weights"] = g.weights
+    if g.hubs is not None:
+        arrays["hubs"] = g.hubs
+    tmp = os.path.join(cdir, f"{g.key}.tmp{os.getpid()}.npz")
+    np.savez(tmp, **arrays)
+    os.replace(tmp, os.path.join(cdir, g.key + ".npz"))
+
+
 def rmat(scale: int, nsamples: int, seed: int, *, symmetrize: bool, weighted: bool = False,
          wmin: int = 1, wmax: int = 100, n_hubs: int = 0, hub_degree: int = 0,
          a: float = RMAT_A, b: float = RMAT_B, c: float = RMAT_C, nthreads: int = 0,
          name: str = "") -> CSR:
     """RMAT graph with self-loops and duplicate entries removed (see module docstring)."""
+    key = _recipe_key(scale=scale, nsamples=nsamples, seed=seed, symmetrize=bool(symmetrize),
+                      weighted=bool(weighted), wmin=wmin, wmax=wmax, n_hubs=n_hubs,
+                      hub_degree=hub_degree, a=a, b=b, c=c)
+    cached = _cache_load(key, name, symmetrize)
+    if cached is not None:
+        return cached
     lib = _load()
     p = _Params(scale, int(symmetrize), nsamples, seed, a, b, c, n_hubs, hub_degree,
                 int(weighted), wmin, wmax, nthreads)
@@ -124,8 +173,10 @@ def rmat(scale: int, nsamples: int, seed: int, *, symmetrize: bool, weighted: bo
                     hubs.ctypes.data if hubs.size else None)
     finally:
         lib.gg_free(h)
-    return CSR(n=n, offsets=off, indices=idx, weights=w, symmetric=symmetrize,
-               hubs=hubs if hubs.size else None, name=name)
+    g = CSR(n=n, offsets=off, indices=idx, weights=w, symmetric=symmetrize,
+            hubs=hubs if hubs.size else None, name=name, key=key)
+    _cache_store(g)
+    return g
 
 
 def edge_weight(seed: int, u: int, v: int, wmin: int = 1, wmax: int = 100) -> int:

@@ -9,6 +9,8 @@ device-side round loop in a CUDA graph).
 Integer results are compared element by element with the CPU oracle (sssp at scale
 24 through the oracle's exact shortest-path certificate plus Dijkstra on a sample
 check); PageRank must be within 1e-5 L1 of the FP64 oracle, and the error is printed.
+With ALB_GRAPH_CACHE / ALB_ORACLE_CACHE set, the graphs and the oracle's results on them are
+read from those directories when present (the cache keys name the generator's recipe).
 """
 import os
 
@@ -63,9 +65,10 @@ def test_rmat22_bfs_sssp(rmat22):
     with make(g) as G:
         o = torch.empty(g.n, dtype=torch.int32, device="cuda")
         G.bfs(src, o)
-        assert np.array_equal(host(o), oracle.bfs(g.n, g.offsets, g.indices, src))
+        assert np.array_equal(host(o), oracle.bfs(g.n, g.offsets, g.indices, src, cache_key=g.key))
         G.sssp(src, o)
-        assert np.array_equal(host(o), oracle.sssp(g.n, g.offsets, g.indices, g.weights, src))
+        assert np.array_equal(host(o), oracle.sssp(g.n, g.offsets, g.indices, g.weights, src,
+                                                   cache_key=g.key))
 
 
 @pytest.fixture(scope="module")
@@ -84,7 +87,7 @@ def test_rmat24_bfs(rmat24):
     got = host(o).copy()
     st = G.stats()
     assert st["hub_rounds"] > 0                 # the LB kernel ran at the default threshold
-    assert np.array_equal(got, oracle.bfs(g.n, g.offsets, g.indices, src))
+    assert np.array_equal(got, oracle.bfs(g.n, g.offsets, g.indices, src, cache_key=g.key))
     # threshold 0 (every active vertex huge) gives the identical result (Sec. 4.1)
     p = G.params()
     G.set_params(hub_threshold=0)
@@ -100,7 +103,7 @@ def test_rmat24_sssp(rmat24):
     G.sssp(src, o)
     d = host(o).copy()
     assert oracle.check_sssp(g.n, g.offsets, g.indices, g.weights, src, d) == -1
-    ref = oracle.sssp(g.n, g.offsets, g.indices, g.weights, src)
+    ref = oracle.sssp(g.n, g.offsets, g.indices, g.weights, src, cache_key=g.key)
     assert np.array_equal(d, ref)
 
 
@@ -108,14 +111,14 @@ def test_rmat24_cc(rmat24):
     g, G = rmat24
     o = torch.empty(g.n, dtype=torch.int32, device="cuda")
     G.cc(o)
-    assert np.array_equal(host(o), oracle.cc(g.n, g.offsets, g.indices))
+    assert np.array_equal(host(o), oracle.cc(g.n, g.offsets, g.indices, cache_key=g.key))
 
 
 def test_rmat24_kcore(rmat24):
     g, G = rmat24
     o = torch.empty(g.n, dtype=torch.int32, device="cuda")
     G.kcore(32, o)
-    assert np.array_equal(host(o), oracle.kcore(g.n, g.offsets, g.indices, 32))
+    assert np.array_equal(host(o), oracle.kcore(g.n, g.offsets, g.indices, 32, cache_key=g.key))
 
 
 def test_rmat24_pagerank(rmat24):
@@ -125,7 +128,7 @@ def test_rmat24_pagerank(rmat24):
     g, G = rmat24
     r = torch.empty(g.n, dtype=torch.float32, device="cuda")
     ref, it_ref, _ = oracle.pagerank(g.n, g.offsets, g.indices, 0.85, 1e-6, 1000,
-                                     assume_symmetric=True, nthreads=NTHREADS)
+                                     assume_symmetric=True, nthreads=NTHREADS, cache_key=g.key)
     p = G.params()
     for t in (p.hub_threshold, 1 << 40):
         G.set_params(hub_threshold=t)
