@@ -125,8 +125,7 @@ typedef struct {
   uint64_t edges_lb;       /* CSR entries expanded by the LB kernel */
   uint64_t pushes;         /* vertices appended to next frontiers */
   double pr_l1;            /* PageRank: L1 change of the last iteration */
-  /* profile = 1 only: summed device time (ms) and launch counts per kernel (ms_other: the init
-   * kernel and, for sssp and cc, the end-of-round frontier compaction) */
+  /* profile = 1 only: summed device time (ms) and launch counts per kernel */
   double ms_inspect, ms_lb, ms_other;
   uint32_t n_inspect, n_lb, n_other, reserved2;
 } alb_stats;

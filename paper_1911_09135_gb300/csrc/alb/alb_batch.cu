@@ -200,9 +200,10 @@ __global__ void __launch_bounds__(kBlock) k_multi_init(TravCtx c) {
   uint32_t* lab = c.args->lab;
   for (uint64_t v = (uint64_t)blockIdx.x * kBlock + threadIdx.x; v < c.n; v += (uint64_t)gridDim.x * kBlock)
     lab[v] = kInf;
-  // sssp: the push bitmap starts empty; bfs: the visited bitmap (the seed kernel sets the sources)
+  // sssp: both push bitmaps start empty; bfs: the visited bitmap (the seed kernel sets the sources)
+  const uint64_t words = APP == APP_SSSP ? 2ull * c.pw : (uint64_t)c.pw;
   if (c.pushed)
-    for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < c.pw; i += (uint64_t)gridDim.x * kBlock)
+    for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < words; i += (uint64_t)gridDim.x * kBlock)
       c.pushed[i] = 0u;
 }
 
@@ -345,7 +346,6 @@ static alb_status add_node(cudaGraphNode_t* node, cudaGraph_t graph, const cudaG
 // threshold rule follows this LB grid.
 struct BatchCfg {
   void *init, *seed, *insp, *lb;
-  void* compact;  // the end-of-round frontier compaction of the marking operator (sssp), or null
   uint32_t seed_grid, seed_block, ib, lbb, threshold;
 };
 
@@ -370,7 +370,6 @@ static BatchCfg batch_cfg(alb_graph g, BatchKind kind) {
     default:
       k.init = (void*)k_multi_init<APP_SSSP>; k.seed = (void*)k_multi_seed<APP_SSSP>;
       k.insp = inspect_for<SsspOp>(g->block); k.lb = lb_for<SsspOp>(g->block);
-      k.compact = (void*)k_compact;
       k.seed_grid = g->blocks; k.seed_block = kBlock;
       break;
   }
@@ -389,7 +388,7 @@ static BatchCfg batch_cfg(alb_graph g, BatchKind kind) {
   return k;
 }
 
-// memset(state) -> init -> seed -> while { inspect -> if (work) lb [-> compact] } [-> transpose]
+// memset(state) -> init -> seed -> while { inspect -> if (work) lb } [-> transpose]
 static alb_status build_batch_graph(alb_graph g, BatchKind kind) {
   BatchWs* b = g->batch;
   cudaGraph_t G = nullptr;
@@ -404,7 +403,7 @@ static alb_status build_batch_graph(alb_graph g, BatchKind kind) {
   void *init = k.init, *seed = k.seed, *insp = k.insp, *lb = k.lb;
   const uint32_t seed_grid = k.seed_grid, seed_block = k.seed_block, ib = k.ib, lbb = k.lbb;
   c.threshold = k.threshold;
-  cudaGraphNode_t n_ms, n_init, n_seed, n_while, n_insp, n_if, n_lb, n_cmp, n_out;
+  cudaGraphNode_t n_ms, n_init, n_seed, n_while, n_insp, n_if, n_lb, n_out;
   cudaMemsetParams ms{};
   ms.dst = g->st;
   ms.value = 0;
@@ -430,9 +429,6 @@ static alb_status build_batch_graph(alb_graph g, BatchKind kind) {
   ip.conditional.size = 1;
   if (cudaGraphAddNode(&n_if, body, &n_insp, nullptr, 1, &ip) != cudaSuccess) return fail(ALB_ERR_CUDA);
   if ((rc = add_node(&n_lb, ip.conditional.phGraph_out[0], nullptr, 0, lb, lbb, g->block, &c)) != ALB_OK)
-    return fail(rc);
-  if (k.compact &&
-      (rc = add_node(&n_cmp, body, &n_if, 1, k.compact, compact_grid(g->n, g->num_sms), kCompactBlock, &c)) != ALB_OK)
     return fail(rc);
   if (kind == BK_MS_BFS || kind == BK_MS_SSSP) {
     if ((rc = add_node(&n_out, G, &n_while, 1, (void*)k_batch_out, g->blocks, kBlock, &c)) != ALB_OK)
@@ -496,13 +492,6 @@ static alb_status batch_host_loop(alb_graph g, BatchKind kind, cudaStream_t s) {
     ALB_CUDA_TRY(cudaStreamSynchronize(s));
     if (g->h_st->hub_packed >> 32) {
       if ((rc = launch(k.lb, k.lbb, g->block, &g->stats.ms_lb, &g->stats.n_lb)) != ALB_OK) return rc;
-      ALB_CUDA_TRY(cudaMemcpyAsync(g->h_st, g->st, sizeof(RoundState), cudaMemcpyDeviceToHost, s));
-      ALB_CUDA_TRY(cudaStreamSynchronize(s));
-    }
-    if (k.compact) {
-      if ((rc = launch(k.compact, compact_grid(g->n, g->num_sms), kCompactBlock, &g->stats.ms_other,
-                       &g->stats.n_other)) != ALB_OK)
-        return rc;
       ALB_CUDA_TRY(cudaMemcpyAsync(g->h_st, g->st, sizeof(RoundState), cudaMemcpyDeviceToHost, s));
       ALB_CUDA_TRY(cudaStreamSynchronize(s));
     }

@@ -98,14 +98,14 @@ static void free_graph_memory(alb_graph g) {
 }
 
 // Launch configuration of application `app` for parameters p.
-// Per-handle round workspace (two frontiers, huge worklist + prefix, one bitmap, state).
+// Per-handle round workspace (two frontiers, huge worklist + prefix, push bitmaps, state).
 static alb_status alloc_workspace(alb_graph g) {
   const size_t nb = sizeof(uint32_t) * (size_t)g->n;
   cudaError_t e = cudaMalloc((void**)&g->F0, nb);
   if (e == cudaSuccess) e = cudaMalloc((void**)&g->F1, nb);
   if (e == cudaSuccess) e = cudaMalloc((void**)&g->hub_v, nb + sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc((void**)&g->hub_p, nb + sizeof(uint32_t));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&g->pushed, sizeof(uint32_t) * (((size_t)g->n + 31) / 32 + 1));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&g->pushed, sizeof(uint32_t) * 2 * (((size_t)g->n + 31) / 32 + 1));
   if (e == cudaSuccess) e = cudaMalloc((void**)&g->st, sizeof(RoundState));
   if (e == cudaSuccess) e = cudaMalloc((void**)&g->args, sizeof(CallArgs));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&g->h_st, sizeof(RoundState));

@@ -32,7 +32,6 @@ struct RoundState {
   unsigned long long hub_packed;   // (huge count << 32) | huge edge total, one atomic per warp
   uint32_t done_inspect;           // last-block tickets
   uint32_t done_lb;
-  uint32_t done_compact;
   uint32_t status;                 // ST_ERR_* bits
   uint32_t all_active;             // round 0 of cc: the frontier is every vertex
   uint32_t hub_rounds;
@@ -73,9 +72,9 @@ struct TravCtx {
   uint32_t* F1;
   uint32_t* hub_v;        // huge worklist "work"
   uint32_t* hub_p;        // exclusive prefix sum of huge degrees ("prefixWork")
-  uint32_t* pushed;       // a bitmap of pw words: bfs's visited vertices, or the vertices marked
-                          // for the next frontier in the current round (sssp, cc)
-  uint32_t pw;            // words of the bitmap: ceil(n / 32)
+  uint32_t* pushed;       // two bitmaps of pw words; bitmap r & 1 marks the vertices pushed in
+                          // round r (dedup of next-frontier pushes, sssp and cc)
+  uint32_t pw;            // words per bitmap: ceil(n / 32)
   RoundState* st;
   const CallArgs* args;
   cudaGraphConditionalHandle h_while;
@@ -133,7 +132,7 @@ struct alb_graph_s {
   uint32_t* F1 = nullptr;
   uint32_t* hub_v = nullptr;
   uint32_t* hub_p = nullptr;
-  uint32_t* pushed = nullptr;       // ceil(n / 32) + 1 words (TravCtx::pushed)
+  uint32_t* pushed = nullptr;       // 2 x ceil(n / 32) words (TravCtx::pushed)
   uint32_t* tmp = nullptr;        // n-entry scratch output when the caller's buffer is host memory
   alb::RoundState* st = nullptr;
   alb::CallArgs* args = nullptr;

@@ -45,32 +45,57 @@ struct BfsOp {
   static constexpr bool kW = false;
   static constexpr bool kVisited = true;
   __device__ static uint32_t sval(const OpArgs&, uint32_t) { return 0u; }
+  __device__ static bool want(const OpArgs&, uint32_t, uint32_t cur, uint32_t) { return cur == kInf; }
+  __device__ static bool commit(const OpArgs& a, uint32_t, uint32_t dst, uint32_t) {
+    return atomicCAS(a.lab + dst, kInf, a.next) == kInf;
+  }
+  // U edges at once: the U CAS are issued before any result is used
+  template <int U>
+  __device__ static void commit_u(const OpArgs& a, const uint32_t (&)[U], const uint32_t (&dst)[U],
+                                  const uint32_t (&)[U], const bool (&w)[U], bool (&push)[U]) {
+    uint32_t old[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) old[u] = w[u] ? atomicCAS(a.lab + dst[u], kInf, a.next) : 0u;
+#pragma unroll
+    for (int u = 0; u < U; ++u) push[u] = w[u] && old[u] == kInf;
+  }
 };
 
-// The min operators (sssp, cc) do not append to the next frontier while they relax: a destination
-// whose label drops only gets its bit set in the push bitmap, and the compaction kernel
-// (k_compact) turns the bitmap into the next frontier at the end of the round. So a vertex is in
-// the next frontier at most once per round, whichever edges improved it, and no relaxation waits
-// for a returned value: U atomicMin, then U reads of the bitmap words, then an atomicOr (whose
-// result is unused) for each bit not yet set; each group is issued before any result is used.
-// The bitmap (1/32 of the labels) stays in L2 next to them.
+// Push of a min operator's destination, at most once per round: the first thread to set the
+// vertex's bit in this round's bitmap pushes it (a plain read of the word skips the atomic when
+// the bit is already set). The bitmaps are 1/32 the size of a per-vertex round stamp, so they and
+// the labels stay in L2 together.
+__device__ __forceinline__ bool claim_push(const OpArgs& a, uint32_t dst) {
+  const uint32_t bit = 1u << (dst & 31u);
+  uint32_t* word = a.pushed + (dst >> 5);
+  return !(*word & bit) && !(atomicOr(word, bit) & bit);
+}
+
+// The min operators' U-edge commit: U non-returning atomicMin, then U bitmap reads, then the
+// atomicOr of the bits not yet set, then the push decisions; each group of memory operations is
+// issued before any of its results is used.
 template <int U, class Cand>
-__device__ __forceinline__ void min_mark_u(const OpArgs& a, const uint32_t (&dst)[U], const bool (&w)[U],
-                                           Cand cand) {
+__device__ __forceinline__ void min_commit_u(const OpArgs& a, const uint32_t (&dst)[U], const bool (&w)[U],
+                                             bool (&push)[U], Cand cand) {
 #pragma unroll
   for (int u = 0; u < U; ++u) if (w[u]) atomicMin(a.lab + dst[u], cand(u));
   uint32_t wd[U];
 #pragma unroll
   for (int u = 0; u < U; ++u) wd[u] = w[u] ? a.pushed[dst[u] >> 5] : 0xFFFFFFFFu;
+  uint32_t old[U];
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const uint32_t bit = 1u << (dst[u] & 31u);
-    if (!(wd[u] & bit)) atomicOr(a.pushed + (dst[u] >> 5), bit);
+    old[u] = (wd[u] & bit) ? bit : atomicOr(a.pushed + (dst[u] >> 5), bit);
   }
+#pragma unroll
+  for (int u = 0; u < U; ++u) push[u] = w[u] && !(old[u] & (1u << (dst[u] & 31u)));
 }
 
-// sssp (push relaxation, Fig. 3): dist[dst] = min(dist[dst], dist[src] + w). A destination whose
-// pre-checked distance improves is marked for the next frontier.
+// sssp (push relaxation, Fig. 3): dist[dst] = min(dist[dst], dist[src] + w).
+// The atomicMin does not wait for its old value: a destination whose pre-checked distance
+// improves is pushed (once per round, by its bit in the round's push bitmap), so every vertex
+// whose distance drops is in the next frontier.
 struct SsspOp {
   static constexpr bool kBatch = false;
   static constexpr bool kW = true;
@@ -79,25 +104,33 @@ struct SsspOp {
   __device__ static bool want(const OpArgs&, uint32_t sv, uint32_t cur, uint32_t w) {
     return (uint64_t)sv + w < (uint64_t)cur;
   }
+  __device__ static bool commit(const OpArgs& a, uint32_t sv, uint32_t dst, uint32_t w) {
+    atomicMin(a.lab + dst, sv + w);
+    return claim_push(a, dst);
+  }
   template <int U>
-  __device__ static void mark_u(const OpArgs& a, const uint32_t (&sv)[U], const uint32_t (&dst)[U],
-                                const uint32_t (&wt)[U], const bool (&w)[U]) {
-    min_mark_u<U>(a, dst, w, [&](int u) { return sv[u] + wt[u]; });
+  __device__ static void commit_u(const OpArgs& a, const uint32_t (&sv)[U], const uint32_t (&dst)[U],
+                                  const uint32_t (&wt)[U], const bool (&w)[U], bool (&push)[U]) {
+    min_commit_u<U>(a, dst, w, push, [&](int u) { return sv[u] + wt[u]; });
   }
 };
 
-// cc (push min-label propagation): label[dst] = min(label[dst], label[src]); the same update and
-// marking as sssp.
+// cc (push min-label propagation): label[dst] = min(label[dst], label[src]); the same
+// non-blocking update and once-per-round push as sssp.
 struct CcOp {
   static constexpr bool kBatch = false;
   static constexpr bool kW = false;
   static constexpr bool kPushBitmap = true;
   __device__ static uint32_t sval(const OpArgs& a, uint32_t u) { return a.lab[u]; }
   __device__ static bool want(const OpArgs&, uint32_t sv, uint32_t cur, uint32_t) { return sv < cur; }
+  __device__ static bool commit(const OpArgs& a, uint32_t sv, uint32_t dst, uint32_t) {
+    atomicMin(a.lab + dst, sv);
+    return claim_push(a, dst);
+  }
   template <int U>
-  __device__ static void mark_u(const OpArgs& a, const uint32_t (&sv)[U], const uint32_t (&dst)[U],
-                                const uint32_t (&)[U], const bool (&w)[U]) {
-    min_mark_u<U>(a, dst, w, [&](int u) { return sv[u]; });
+  __device__ static void commit_u(const OpArgs& a, const uint32_t (&sv)[U], const uint32_t (&dst)[U],
+                                  const uint32_t (&)[U], const bool (&w)[U], bool (&push)[U]) {
+    min_commit_u<U>(a, dst, w, push, [&](int u) { return sv[u]; });
   }
 };
 
@@ -117,6 +150,7 @@ struct KcoreOp {
     const uint32_t old = atomicSub(a.lab + dst, cnt);
     return old >= a.k && old - cnt < a.k;
   }
+  __device__ static bool commit(const OpArgs& a, uint32_t, uint32_t dst, uint32_t) { return commit_n(a, dst, 1u); }
 };
 
 template <class Op, class = void>
@@ -124,17 +158,18 @@ struct uses_visited { static constexpr bool value = false; };
 template <class Op>
 struct uses_visited<Op, decltype(void(Op::kVisited))> { static constexpr bool value = Op::kVisited; };
 
+// The bitmap an operator's OpArgs carries in round parity `cur`: the round's push bitmap, or the
+// traversal-wide visited bitmap (bitmap 0).
+template <class Op>
+__device__ __forceinline__ uint32_t* op_bitmap(const TravCtx& c, uint32_t cur) {
+  if (!c.pushed) return nullptr;
+  return uses_visited<Op>::value ? c.pushed : c.pushed + (size_t)cur * c.pw;
+}
+
 template <class Op, class = void>
 struct uses_push_bitmap { static constexpr bool value = false; };
 template <class Op>
 struct uses_push_bitmap<Op, decltype(void(Op::kPushBitmap))> { static constexpr bool value = Op::kPushBitmap; };
-
-// The bitmap an operator's OpArgs carries: the traversal-wide visited bitmap (bfs) or the push
-// bitmap of the round being expanded (sssp, cc; the compaction kernel empties it again).
-template <class Op>
-__device__ __forceinline__ uint32_t* op_bitmap(const TravCtx& c) {
-  return (uses_visited<Op>::value || uses_push_bitmap<Op>::value) ? c.pushed : nullptr;
-}
 
 template <class Op, class = void>
 struct aggregates { static constexpr bool value = false; };
@@ -306,14 +341,14 @@ __device__ __forceinline__ void relax(const TravCtx& c, const OpArgs& a, const u
       if (push[u]) a.lab[dst[u]] = a.next;
     push_n<U>(push, dst, sink);
   } else {
-    static_assert(uses_push_bitmap<Op>::value, "a single-source operator is visited, counted or marked");
     uint32_t cur[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) cur[u] = ok[u] ? a.lab[dst[u]] : 0u;
-    bool w[U];
+    bool w[U], push[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) w[u] = ok[u] && Op::want(a, sv[u], cur[u], wt[u]);
-    Op::template mark_u<U>(a, sv, dst, wt, w);
+    Op::template commit_u<U>(a, sv, dst, wt, w, push);
+    push_n<U>(push, dst, sink);
   }
 }
 
@@ -337,7 +372,6 @@ static __device__ void finish_round(const TravCtx& c) {
   st->tile_next = 0u;
   st->done_inspect = 0u;
   st->done_lb = 0u;
-  st->done_compact = 0u;
   st->all_active = 0u;
   st->round = r + 1u;
   bool go = nextc > 0u;
@@ -412,8 +446,7 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_inspe
   constexpr int UC = Op::kBatch ? kUMs : kUCta;  // edges in flight per thread, per bin
   constexpr int UW = Op::kBatch ? kUMs : kUWarp;
   constexpr int UT = Op::kBatch ? (kUMs < kUThread ? kUMs : kUThread) : kUThread;
-  constexpr bool kSink = !uses_push_bitmap<Op>::value;  // marking operators push nothing here
-  __shared__ uint32_t s_push[kSink ? kTilePushBuf : 1];  // the tile's pushes (PushSink)
+  __shared__ uint32_t s_push[kTilePushBuf];  // the tile's pushes (PushSink)
   constexpr uint32_t kMap = kOwnerMapOf<Op, B>;
   __shared__ uint16_t s_own[kMap];  // thread-bin edge position -> the thread (vertex) owning it
   __shared__ uint32_t s_npush, s_pbase;
@@ -436,10 +469,17 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_inspe
   uint32_t* Fn = cur ? c.F0 : c.F1;
   uint32_t* ncount = &st->fcount[cur ^ 1u];
   const CallArgs* ca = c.args;
-  const OpArgs a{ca->lab, op_bitmap<Op>(c), r + 1u, ca->k, ca->aux, c.n, c.chk};
+  const OpArgs a{ca->lab, op_bitmap<Op>(c, cur), r + 1u, ca->k, ca->aux, c.n, c.chk};
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   unsigned long long twc_edges = 0ull;
   const PushSink sink{Fn, ncount, c.n, c.chk, s_push, &s_npush, kTilePushBuf};
+  if constexpr (uses_push_bitmap<Op>::value) {
+    // the other bitmap (last round's) is cleared for the next round
+    if (c.pushed) {
+      uint32_t* other = c.pushed + (size_t)(cur ^ 1u) * c.pw;
+      for (uint32_t i = blockIdx.x * B + tid; i < c.pw; i += gridDim.x * B) other[i] = 0u;
+    }
+  }
   if constexpr (Op::kBatch) Op::round_start(a, r);  // multi-source operators' per-round state
 
   // Tiles of B frontier entries, taken dynamically. Tile t is made of the 32-entry chunks
@@ -545,7 +585,7 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_inspe
       relax<Op, UT>(c, a, e, ok, s2, sink, hk, hc);
     }
     __syncthreads();
-    if constexpr (kSink) push_flush(sink, &s_pbase);
+    push_flush(sink, &s_pbase);
   }
   if constexpr (kHot) {
     // apply the CTA's pending counts: one atomic per target; the one that crosses k pushes it
@@ -569,7 +609,7 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_inspe
     const unsigned long long hp = __ldcg(&st->hub_packed);
     const uint32_t nh = (uint32_t)(hp >> 32);
     if (c.use_graph) cudaGraphSetConditional(c.h_if, nh > 0u ? 1u : 0u);
-    if (nh == 0u && !uses_push_bitmap<Op>::value) finish_round(c);  // else k_compact closes it
+    if (nh == 0u) finish_round(c);
   }
 }
 
@@ -584,8 +624,7 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_lb(Tr
   __shared__ uint32_t s_base[kStage];
   __shared__ uint32_t s_val[kStage];
   __shared__ uint32_t s_src[kTrace ? kStage : 1];
-  constexpr bool kSink = !kTrace && !uses_push_bitmap<Op>::value;  // marking operators push nothing here
-  __shared__ uint32_t s_push[kSink ? kPushBufOf<B> : 1];  // one step's pushes (PushSink)
+  __shared__ uint32_t s_push[kTrace ? 1 : kPushBufOf<B>];  // one step's pushes (PushSink)
   __shared__ uint32_t s_npush, s_pbase;
 
   RoundState* st = c.st;
@@ -602,12 +641,12 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_lb(Tr
   uint32_t* Fn = cur ? c.F0 : c.F1;
   uint32_t* ncount = &st->fcount[cur ^ 1u];
   const CallArgs* ca = c.args;
-  const OpArgs a{ca->lab, op_bitmap<Op>(c), r + 1u, ca->k, ca->aux, c.n, c.chk};
+  const OpArgs a{ca->lab, op_bitmap<Op>(c, cur), r + 1u, ca->k, ca->aux, c.n, c.chk};
   const uint32_t tid = threadIdx.x, lane = tid & 31u;
   // a step of the CTA is B x U positions, at most one push each: the buffer never overflows
-  static_assert(!kSink || B * (Op::kBatch ? kUMs : kULb) <= kPushBufOf<B>,
+  static_assert(kTrace || B * (Op::kBatch ? kUMs : kULb) <= kPushBufOf<B>,
                 "one LB step's pushes must fit the CTA buffer");
-  const PushSink sink{Fn, ncount, c.n, c.chk, kSink ? s_push : nullptr, &s_npush, kSink ? kPushBufOf<B> : 0u};
+  const PushSink sink{Fn, ncount, c.n, c.chk, kTrace ? nullptr : s_push, &s_npush, kPushBufOf<B>};
   if (threadIdx.x == 0) s_npush = 0u;
 
   const bool staged = nh <= (uint32_t)kStage;
@@ -694,18 +733,12 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_lb(Tr
   // after each CTA-uniform step: the step's staged pushes go to the frontier in one atomic (and,
   // between the two barriers, the next step's slot starts are found)
   auto flush = [&](uint64_t next_c0) {
-    if constexpr (kSink) {
+    if constexpr (!kTrace) {
       __syncthreads();
       push_flush(sink, &s_pbase);
       if (threadIdx.x == 0) s_npush = 0u;  // every thread read the count inside push_flush
       if (shared_search) slot_starts(next_c0);
       __syncthreads();
-    } else if constexpr (!kTrace) {
-      if (shared_search) {  // CTA-uniform
-        __syncthreads();
-        slot_starts(next_c0);
-        __syncthreads();
-      }
     }
   };
   if (c.distribution == 0u) {
@@ -746,60 +779,8 @@ __global__ void __launch_bounds__(B, (round_kernel_min_blocks<Op, B>())) k_lb(Tr
     if (lane == 0 && lb_edges) atomicAdd(c.cta_lb + blockIdx.x, lb_edges);
   }
   if (last_block_ticket(&st->done_lb)) {
-    if constexpr (!kTrace && !uses_push_bitmap<Op>::value) finish_round(c);  // else k_compact closes it
+    if constexpr (!kTrace) finish_round(c);
   }
-}
-
-// ------------------------------------------------------ frontier compaction
-
-// End of a round of the marking operators (sssp, cc): the push bitmap becomes the next frontier
-// and is emptied for the next round. Each CTA takes kCompactBlock words at a time (one per
-// thread, coalesced); a block scan of their bit counts gives each word its run of slots, one
-// global atomic per chunk reserves the chunk's run in the frontier, and the ids are staged in
-// shared memory and stored coalesced. Only non-zero words are written back. The frontier comes
-// out in ascending order within each chunk of 32 x kCompactBlock vertex ids, so neighbouring
-// frontier entries of the next round read neighbouring degrees and labels. The last CTA closes
-// the round.
-constexpr int kCompactBlock = 256;
-constexpr uint32_t kCompactPerSm = 4;  // resident CTAs per SM the grid is sized for (33 KB each)
-
-static __global__ void __launch_bounds__(kCompactBlock) k_compact(TravCtx c) {
-  constexpr int B = kCompactBlock;
-  __shared__ uint32_t s_ids[32 * B];
-  __shared__ uint32_t s_warp[B / 32 + 1];
-  __shared__ uint32_t s_base;
-  RoundState* st = c.st;
-  const uint32_t cur = st->round & 1u;
-  uint32_t* Fn = cur ? c.F0 : c.F1;
-  uint32_t* ncount = &st->fcount[cur ^ 1u];
-  uint32_t* bm = c.pushed;
-  const uint32_t tid = threadIdx.x;
-  for (uint64_t w0 = (uint64_t)blockIdx.x * B; w0 < c.pw; w0 += (uint64_t)gridDim.x * B) {  // CTA-uniform
-    const uint64_t wi = w0 + tid;
-    uint32_t word = wi < c.pw ? bm[wi] : 0u;  // bits of ids >= n are never set
-    uint32_t total;
-    const uint32_t ex = block_exclusive_scan<B>((uint32_t)__popc(word), s_warp, &total);
-    if (total == 0u) continue;  // CTA-uniform
-    if (word) bm[wi] = 0u;
-    const uint32_t vb = (uint32_t)wi << 5;
-    for (uint32_t q = ex; word; word &= word - 1u) s_ids[q++] = vb + (uint32_t)(__ffs(word) - 1);
-    if (tid == 0) s_base = atomicAdd(ncount, total);
-    __syncthreads();
-    const uint32_t b = s_base;
-    for (uint32_t j = tid; j < total; j += B) {
-      const uint32_t g = b + j;
-      if (ALB_IN_RANGE(c.chk, CHK_PUSH, g, c.n)) Fn[g] = s_ids[j];
-    }
-    __syncthreads();  // s_ids and s_base are reused by the next chunk
-  }
-  if (last_block_ticket(&st->done_compact)) finish_round(c);
-}
-
-// k_compact's grid for n vertices: one CTA per chunk of words, at most kCompactPerSm per SM.
-static inline uint32_t compact_grid(uint32_t n, int num_sms) {
-  const uint64_t chunks = (((uint64_t)n + 31) / 32 + kCompactBlock - 1) / kCompactBlock;
-  const uint64_t cap = (uint64_t)(num_sms > 0 ? num_sms : 1) * kCompactPerSm;
-  return (uint32_t)(chunks < 1 ? 1 : (chunks < cap ? chunks : cap));
 }
 
 // ------------------------------------------------------------- init kernels
@@ -825,8 +806,8 @@ __global__ void __launch_bounds__(kBlock) k_init(TravCtx c) {
       warp_append(ok && d < k, v, c.F0, &st->fcount[0], c.n, c.chk);
     }
   }
-  if constexpr (APP == APP_SSSP || APP == APP_CC) {  // the push bitmap starts empty
-    for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < c.pw; i += (uint64_t)gridDim.x * kBlock)
+  if constexpr (APP == APP_SSSP || APP == APP_CC) {  // both push bitmaps start empty
+    for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < 2ull * c.pw; i += (uint64_t)gridDim.x * kBlock)
       c.pushed[i] = 0u;
   }
   if constexpr (APP == APP_BFS) {  // the visited bitmap starts with the source alone

@@ -70,9 +70,6 @@ static void* lb_fn(App app, uint32_t B) {
     default: return nullptr;
   }
 }
-// sssp and cc mark the next frontier in a bitmap, which k_compact turns into the frontier
-static bool marks(App app) { return app == APP_SSSP || app == APP_CC; }
-
 static void* init_fn(App app) {
   switch (app) {
     case APP_BFS: return (void*)k_init<APP_BFS>;
@@ -142,8 +139,7 @@ static alb_status add_kernel(cudaGraphNode_t* node, cudaGraph_t graph, const cud
   return ALB_OK;
 }
 
-// memset(state) -> init -> while(frontier non-empty) { inspect -> if(work) { lb } [-> compact] }
-// [-> kcore finish]
+// memset(state) -> init -> while(frontier non-empty) { inspect -> if(work) { lb } } [-> kcore finish]
 // L2 persistence for the label array (alb_params.l2_persist_fraction > 0, CUDA-graph mode): the
 // labels live in the handle's own buffer, whose address the cached graph can hold, and are copied
 // to the caller's buffer at the end of the call; the round kernels' nodes carry an access-policy
@@ -184,7 +180,7 @@ static alb_status build_graph(alb_graph g, App app) {
     return fail(ALB_ERR_CUDA);
   TravCtx c = make_ctx(g, true, hw, hi);
 
-  cudaGraphNode_t n_ms, n_init, n_while, n_insp, n_if, n_lb, n_cmp, n_fin;
+  cudaGraphNode_t n_ms, n_init, n_while, n_insp, n_if, n_lb, n_fin;
   cudaMemsetParams ms{};
   ms.dst = g->st;
   ms.value = 0;
@@ -211,10 +207,6 @@ static alb_status build_graph(alb_graph g, App app) {
   if (cudaGraphAddNode(&n_if, body, &n_insp, nullptr, 1, &ip) != cudaSuccess) return fail(ALB_ERR_CUDA);
   cudaGraph_t ifbody = ip.conditional.phGraph_out[0];
   if ((rc = add_kernel(&n_lb, ifbody, nullptr, 0, lb_fn(app, g->block), g->lb_blocks, &c, g->block)) != ALB_OK)
-    return fail(rc);
-  if (marks(app) &&
-      (rc = add_kernel(&n_cmp, body, &n_if, 1, (void*)k_compact, compact_grid(g->n, g->num_sms), &c,
-                       kCompactBlock)) != ALB_OK)
     return fail(rc);
   if (persist_labels(g)) {
     cudaKernelNodeAttrValue v{};
@@ -303,16 +295,6 @@ static alb_status host_loop(alb_graph g, App app, cudaStream_t s) {
       ALB_CUDA_TRY(cudaLaunchKernel(lb_fn(app, g->block), dim3(g->lb_blocks), dim3(g->block), args, 0, s));
       g->stats.ms_lb += t.stop();
       g->stats.n_lb += 1;
-      ALB_CUDA_TRY(cudaMemcpyAsync(g->h_st, g->st, sizeof(RoundState), cudaMemcpyDeviceToHost, s));
-      ALB_CUDA_TRY(cudaStreamSynchronize(s));
-    }
-    if (marks(app)) {
-      Timer t(prof, s);
-      void* args[] = {&c};
-      ALB_CUDA_TRY(cudaLaunchKernel((void*)k_compact, dim3(compact_grid(g->n, g->num_sms)), dim3(kCompactBlock),
-                                    args, 0, s));
-      g->stats.ms_other += t.stop();
-      g->stats.n_other += 1;
       ALB_CUDA_TRY(cudaMemcpyAsync(g->h_st, g->st, sizeof(RoundState), cudaMemcpyDeviceToHost, s));
       ALB_CUDA_TRY(cudaStreamSynchronize(s));
     }
