@@ -166,8 +166,8 @@ def test_rmat22_batch_of_128_sources(rmat22):
                 oracle.check_sssp(g.n, g.offsets, g.indices, g.weights, s, ds[i]))
 
     with ThreadPoolExecutor(max_workers=NTHREADS) as ex:
-        verdicts = list(ex.map(certify, range(128)))
-    bad = [(i, v) for i, v in enumerate(verdicts) if v != (-1, -1)]
+        certs = list(ex.map(certify, range(128)))
+    bad = [(i, v) for i, v in enumerate(certs) if v != (-1, -1)]
     assert not bad, bad[:8]
     for i in (0, 127):
         s = int(srcs[i])
