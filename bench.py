@@ -766,25 +766,46 @@ def batch_arm(args, dist):
                 for i, s in enumerate(srcs.tolist()):
                     single(G.h, s, out[i * n:(i + 1) * n])
             ms_plain = timed(plain, max(1, args.steps // 2))
-            # the batched path gets its own threshold (multi-source rounds relax every active
-            # source of an edge, so the best split between TWC and the LB kernel can differ),
-            # chosen by timing a batch of 128 other sources; the TWC cut-offs stay the tuned ones
-            cand = sorted({int(tuned.hub_threshold), -1, 1 << 12, 1 << 14, 1 << 16, 1 << 18})
-            trial = {}
+            # the batched path gets its own knobs (multi-source rounds relax every active source
+            # of an edge, so the best split between TWC and the LB kernel, the CTA size and the
+            # TWC cut-offs can differ), chosen one after another by timing a batch of 128 other
+            # sources: the threshold, then the CTA size, then the cut-offs
+            def trial_of(**kw):
+                G.set_app_params(app, **kw)
+                return timed(lambda: batch(G.h, d_tsrcs, 128, out), 1)
             if args.batch_threshold is not None:
                 t_best = args.batch_threshold
+                G.set_app_params(app, hub_threshold=t_best)
+                bknobs = {"block_size": tuned.block_size, "twc_cta_min": tuned.twc_cta_min,
+                          "twc_warp_min": tuned.twc_warp_min}
             else:
-                for t in cand:
-                    G.set_app_params(app, hub_threshold=t)
-                    trial[t] = timed(lambda: batch(G.h, d_tsrcs, 128, out), 1)
+                cand = sorted({int(tuned.hub_threshold), -1, 1 << 12, 1 << 14, 1 << 16, 1 << 18})
+                trial = {t: trial_of(hub_threshold=t) for t in cand}
                 t_best = min(trial, key=trial.get)
-            G.set_app_params(app, hub_threshold=t_best)
+                G.set_app_params(app, hub_threshold=t_best)
+                best = trial[t_best]
+                bknobs = {"block_size": tuned.block_size, "twc_cta_min": tuned.twc_cta_min,
+                          "twc_warp_min": tuned.twc_warp_min}
+                for b in (128, 256, 512):
+                    if b == bknobs["block_size"]:
+                        continue
+                    ms = trial_of(block_size=b)
+                    if ms < best:
+                        best, bknobs["block_size"] = ms, b
+                G.set_app_params(app, block_size=bknobs["block_size"])
+                for cm, wm in ((128, 16), (256, 32), (512, 64), (1024, 64), (2048, 128)):
+                    if (cm, wm) == (bknobs["twc_cta_min"], bknobs["twc_warp_min"]):
+                        continue
+                    ms = trial_of(twc_cta_min=cm, twc_warp_min=wm)
+                    if ms < best:
+                        best, bknobs["twc_cta_min"], bknobs["twc_warp_min"] = ms, cm, wm
+                G.set_app_params(app, hub_threshold=t_best, **bknobs)
             ms_batch = timed(lambda: batch(G.h, d_srcs, 128, out), args.steps)
             res[app] = {"queries": 128, "ms_plain": round(ms_plain, 3), "ms_batched": round(ms_batch, 3),
                         "speedup": round(ms_plain / ms_batch, 2),
                         "autotuned": {"hub_threshold": tuned.hub_threshold, "twc_cta_min": tuned.twc_cta_min,
                                       "twc_warp_min": tuned.twc_warp_min, "block_size": tuned.block_size},
-                        "batched_hub_threshold": t_best,
+                        "batched_hub_threshold": t_best, "batched_knobs": bknobs,
                         "queries_per_s_batched": round(128 / (ms_batch * 1e-3), 1)}
         # rounds of the last group of the timed batch (sssp), for the round-overhead estimate below
         rounds_group = G.stats()["rounds"] if "sssp" in res else None
